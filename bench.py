@@ -1,0 +1,371 @@
+"""Benchmark: Mpaths/s and ms/frame of the tet-grid path tracer at 1024^2, 32 spp.
+
+Workload: the production scene -- a 1024 x 1024 x 512 sparse fBm x Worley
+cloud (synthetic, seeded), adaptive LEB grid for the 1024^2 view at a 1-pixel
+footprint, BF16 densities, albedo 0.95, HG g = 0.7, up to 128 bounces, sun and
+environment light.  A step renders one 1024^2 x 32 spp frame (33.5 M paths)
+on the grid, which is built once before timing (its build time is reported
+separately and is part of the end-to-end number).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--scene NAME]
+
+Under torchrun each rank renders the frame with its own range of samples
+(no data-path collective): weak scaling.  --impl reference times the CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpaths/s & ms/frame @1024² 32spp; time-to-equal-RMSE cached vs plain"
+BYTES_PER_STEP = 32          # one 32-byte record (one DRAM sector) per tet step, shadow steps included
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scene", default="production")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-px", type=int, default=0, help="side of the oracle's pixel window (0: auto)")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    for path in (os.path.join(ROOT, "MEASURED_PEAKS.json"),):
+        if os.path.exists(path):
+            with open(path) as fh:
+                d = json.load(fh)
+            return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.path.join("/tmp", "tetvol_clocks_%d.csv" % os.getpid()), "w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        self.out.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                s, m = float(r[1]), float(r[2])
+            except (ValueError, IndexError):
+                continue
+            sm.append(s)
+            mx = max(mx, m)
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2506_11510_gb300", "csrc")
+    for f in ("estimator.cuh", "walk_tet.cuh", "common.cuh", "render.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(scene_name):
+    """DRAM bytes per render launch from the committed ncu summary, if it was taken
+    on the current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "k_estimate_%s_traffic.json" % scene_name)
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("kernel_digest") != kernel_source_digest():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def workload_name(s, ntets):
+    nx, ny, nz = s.dims
+    return ("%s: %dx%dx%d procedural cloud, adaptive LEB grid (%d tets, %s density), %dx%d @ %d spp, "
+            "albedo %.2f, g %.1f, <= %d bounces" % (s.name, nx, ny, nz, ntets,
+                                                     {0: "FP32", 1: "BF16", 2: "FP16"}[s.density_format],
+                                                     s.camera.width, s.camera.height, s.spp, s.medium.albedo,
+                                                     s.medium.g, s.medium.max_bounces))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2506_11510_gb300 as tv
+    from paper_2506_11510_gb300 import _build, workloads as W
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    dev = torch.device("cuda", local if ws > 1 else torch.cuda.current_device())
+    s = W.scene(args.scene)
+    st = torch.cuda.current_stream()
+
+    vol = W.make_volume(s, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    grid = tv.build_scene_grid(s, vol)
+    torch.cuda.synchronize()
+    build_ms = (time.time() - t0) * 1e3
+    ntets = grid.info.num_tets
+
+    W_, H_ = s.camera.width, s.camera.height
+    img = torch.zeros((H_, W_), dtype=torch.float32, device=dev)
+    img2 = torch.zeros_like(img)
+    stats = tv.new_stats(dev)
+    spp = s.spp
+    offset = rank * spp                                   # each rank its own samples
+
+    for _ in range(args.warmup):
+        tv.tet_render(grid, s.camera, s.medium, spp, s.render_seed, offset, img, img2)
+    torch.cuda.synchronize()
+
+    # counters of one frame (identical every frame: same paths)
+    stats.zero_()
+    tv.tet_render(grid, s.camera, s.medium, spp, s.render_seed, offset, img, img2, stats=stats)
+    torch.cuda.synchronize()
+    counters = tv.stats_dict(stats)
+    steps_per_frame = counters["tet_steps"] + counters["shadow_steps"]
+
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e_all0, e_all1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_all0.record(st)
+    for i in range(args.steps):
+        ev[i][0].record(st)
+        tv.tet_render(grid, s.camera, s.medium, spp, s.render_seed, offset, img, img2)
+        ev[i][1].record(st)
+    e_all1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = e_all0.elapsed_time(e_all1)
+    per_launch = [a.elapsed_time(b) for a, b in ev]
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    paths = float(W_ * H_ * spp)
+    value = paths * ws * args.steps / (total_ms * 1e-3) / 1e6
+
+    # end to end through the public API: host volume -> device, build, render, image -> host
+    e2e = None
+    if args.e2e_steps > 0:
+        host_vol = vol.cpu().pin_memory()
+        out_sum = torch.empty((H_, W_), dtype=torch.float32).pin_memory()
+        out_sq = torch.empty_like(out_sum).pin_memory()
+        del grid
+        torch.cuda.empty_cache()
+        times = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            dvol = host_vol.to(dev, non_blocking=True)
+            g2 = tv.build_scene_grid(s, dvol)
+            a, b = tv.tet_render(g2, s.camera, s.medium, spp, s.render_seed, offset)
+            out_sum.copy_(a, non_blocking=True)
+            out_sq.copy_(b, non_blocking=True)
+            torch.cuda.synchronize()
+            times.append(time.time() - t0)
+            del g2, dvol
+        e2e_s = sum(times) / len(times)
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": round(paths * ws / e2e_s / 1e6, 3), "unit": "Mpaths/s",
+               "h2d_bytes_per_step": int(host_vol.numel() * 4), "d2h_bytes_per_step": int(2 * out_sum.numel() * 4),
+               "ms_per_step": round(e2e_s * 1e3, 2),
+               "includes": "volume upload, LEB build, frame render, image download"}
+
+    peak, peak_kind = load_peaks()
+    mean_launch_ms = sum(per_launch) / len(per_launch)
+    achieved = steps_per_frame * BYTES_PER_STEP / (mean_launch_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(args.scene)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_estimate<TetWalker> (persistent path tracer)",
+                "algorithmic_bytes": "32 B per tet step x %d steps per launch" % steps_per_frame,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
+                "fallback 6.8 TB/s"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, s, vol)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "Mpaths/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded procedural volume; stands in for the paper's OpenVDB assets)",
+                "config": {"workload": workload_name(s, ntets), "ms_per_frame": round(ms_per_step, 3),
+                           "tets": ntets, "grid_depth": grid_max_depth(ntets, s), "build_ms": round(build_ms, 1),
+                           "width": W_, "height": H_, "spp": spp, "paths_per_frame": int(paths),
+                           "tet_steps_per_path": round(steps_per_frame / paths, 2),
+                           "collisions_per_path": round(counters["collisions"] / paths, 3),
+                           "density_storage": {0: "fp32", 1: "bf16", 2: "fp16"}[s.density_format],
+                           "l2": "inputs larger than L2: grid records %.2f GB" % (ntets * 32 / 1e9),
+                           "parallelism": "one frame per rank, disjoint sample ranges"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def grid_max_depth(ntets, s):
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU) on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(s, vol_np, side, nthreads=0):
+    """Oracle grid for a side x side pixel window at the centre of the frame (the
+    camera criterion refines the window's sub-frustum only) and the window's
+    paths at the frame's spp.  Returns (paths, render seconds, build seconds)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2506_11510_gb300 import workloads as W
+    cam = s.camera
+    frac = side / cam.height
+    fov = 2 * math.degrees(math.atan(math.tan(math.radians(cam.fov_y_deg) / 2) * frac))
+    wcam = W.Camera(cam.pos, cam.target, cam.up, fov, side, side)
+    t0 = time.time()
+    g = O.Grid.for_scene(s, vol_np, camera=wcam, nthreads=nthreads)
+    tb = time.time() - t0
+    py, px, sm = np.meshgrid(np.arange(side), np.arange(side), np.arange(s.spp), indexing="ij")
+    t0 = time.time()
+    g.render_paths(wcam, s.medium, s.render_seed, px.ravel(), py.ravel(), sm.ravel(), nthreads=nthreads)
+    tr = time.time() - t0
+    return side * side * s.spp, tr, tb
+
+
+def cpu_baseline(args, s, vol):
+    vol_np = vol.cpu().numpy() if hasattr(vol, "cpu") else vol
+    cores = os.cpu_count() or 1
+    side = args.cpu_sample_px or 16
+    paths, tr, tb = oracle_sample(s, vol_np, side)
+    # grow the window until the render takes ~10 s of wall time (bounded)
+    while tr < 3.0 and side < 128 and not args.cpu_sample_px:
+        side *= 2
+        paths, tr, tb = oracle_sample(s, vol_np, side)
+    return {"value": round(paths / tr / 1e6, 5), "unit": "Mpaths/s", "cores": cores, "kind": "oracle",
+            "sample": "%dx%d-pixel window at the frame centre, %d spp (%d paths), on the oracle's grid for the "
+                      "window's sub-frustum (built in %.1f s, not timed); fp64 C++, OpenMP over paths"
+                      % (side, side, s.spp, paths, tb),
+            "render_s": round(tr, 2)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2506_11510_gb300 import workloads as W
+    s = W.scene(args.scene)
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+    except Exception:
+        dev = "cpu"
+    vol = W.make_volume(s, device=dev).cpu().numpy()
+    side = args.cpu_sample_px or 16
+    for _ in range(args.warmup):
+        pass
+    times, paths = [], 0
+    for _ in range(max(1, args.steps)):
+        paths, tr, tb = oracle_sample(s, vol, side)
+        times.append(tr)
+    mean = sum(times) / len(times)
+    value = paths / mean / 1e6
+    cores = os.cpu_count() or 1
+    line = {"metric": METRIC, "value": round(value, 5), "unit": "Mpaths/s", "n_gpus": ws, "steps": len(times),
+            "warmup": args.warmup, "ms_per_step": round(mean * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_name(s, 0) + " -- oracle on a %dx%d-pixel window" % (side, side)},
+            "cpu_baseline": {"value": round(value, 5), "unit": "Mpaths/s", "cores": cores, "kind": "oracle",
+                             "sample": "%dx%d-pixel window, %d spp per step" % (side, side, s.spp)},
+            "e2e": {"value": round(value, 5), "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,838 @@
+// leb_build: the adaptive conforming grid of Sec. 2 on the GPU.
+//
+// Leaves live in structure-of-arrays form and are rebuilt every round by a
+// stable compaction in which a split leaf is replaced, in place, by its two
+// children (bit 0 then bit 1).  Starting from the roots in code order this
+// keeps the leaves in depth-first order of their LEB codes at every round, so
+// the final grid needs no sort.
+//
+// Round: (1) mark = criterion || hanging vertex (one of the six edge
+// midpoints is a vertex of the grid, found in an open-addressing hash set of
+// packed vertex coordinates); (2) exclusive scan of the marks gives every leaf
+// its output slot; (3) split / copy, inserting the new vertices; (4) the
+// density statistics of the new leaves are gathered by warps over chunks of
+// their voxel bounding boxes (exact integer inside tests against the four face
+// planes), then the criterion is evaluated once per new leaf.
+// Finalize: faces are matched through a hash of their vertex sums (verified
+// against the full vertex triples), then the 32-byte records are packed.
+#include <cub/device/device_scan.cuh>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tv {
+
+namespace {
+
+constexpr unsigned long long EMPTY = ~0ull;
+constexpr int TPB = 256;
+constexpr int CHUNK = 256;          // voxels per warp work item of the statistics pass
+
+struct Geo {
+  int nx, ny, nz, n, m, K, max_depth;
+  int C[3];
+  int h;                            // voxel i has its centre at (2i + 1) h, units of 2^-K cube
+};
+
+struct CamD {
+  int on;
+  double eye[3], f[3], r[3], u[3];
+  double tanF, tanX, near_g, thr;
+};
+
+struct Crit {
+  Geo g;
+  CamD cam;
+  int var_on;
+  unsigned long long theta_q16;
+};
+
+struct LeafPtrs {
+  int4* v;                          // 3 int4 per leaf: x0 x1 x2 x3
+  unsigned long long* code;
+  uint8_t* tag;
+  uint32_t *cnt, *mn, *mx;
+  unsigned long long* sum;
+  uint8_t* crit;
+};
+
+struct Leaves {
+  DevBuf<int4> v;
+  DevBuf<unsigned long long> code, sum;
+  DevBuf<uint8_t> tag, crit;
+  DevBuf<uint32_t> cnt, mn, mx;
+  size_t cap = 0;
+  void ensure(size_t n) {
+    if (n <= cap) return;
+    size_t c = std::max<size_t>(n + n / 2, 1024);
+    v.alloc(3 * c); code.alloc(c); sum.alloc(c); tag.alloc(c); crit.alloc(c); cnt.alloc(c); mn.alloc(c); mx.alloc(c);
+    cap = c;
+  }
+  LeafPtrs ptrs() { return LeafPtrs{v.p, code.p, tag.p, cnt.p, mn.p, mx.p, sum.p, crit.p}; }
+};
+
+__device__ __forceinline__ unsigned long long mix(unsigned long long k) {
+  k ^= k >> 31; k *= 0x7FB5D329728EA185ull;
+  k ^= k >> 27; k *= 0x81DADEF4BC2DD44Dull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ unsigned long long pack3(long long x, long long y, long long z) {
+  return (unsigned long long)x | ((unsigned long long)y << 21) | ((unsigned long long)z << 42);
+}
+
+// Insert-if-absent into an open-addressing set; returns the slot, or -1 after
+// probing every slot without success (a full table: the caller flags an error).
+__device__ __forceinline__ long long hset_insert(unsigned long long* keys, unsigned long long mask,
+                                                 unsigned long long key, unsigned long long* count) {
+  unsigned long long s = mix(key) & mask;
+  for (unsigned long long probe = 0; probe <= mask; ++probe) {
+    const unsigned long long prev = atomicCAS(keys + s, EMPTY, key);
+    if (prev == EMPTY) { if (count) atomicAdd(count, 1ull); return (long long)s; }
+    if (prev == key) return (long long)s;
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+
+// Slot of key, or -1 when absent (an empty slot, or every slot probed).
+__device__ __forceinline__ long long hset_find(const unsigned long long* keys, unsigned long long mask,
+                                               unsigned long long key) {
+  unsigned long long s = mix(key) & mask;
+  for (unsigned long long probe = 0; probe <= mask; ++probe) {
+    const unsigned long long k = keys[s];
+    if (k == key) return (long long)s;
+    if (k == EMPTY) return -1;
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void load_tet(const int4* v, long long i, int x[4][3]) {
+  const int4 a = v[3 * i], b = v[3 * i + 1], c = v[3 * i + 2];
+  x[0][0] = a.x; x[0][1] = a.y; x[0][2] = a.z; x[1][0] = a.w;
+  x[1][1] = b.x; x[1][2] = b.y; x[2][0] = b.z; x[2][1] = b.w;
+  x[2][2] = c.x; x[3][0] = c.y; x[3][1] = c.z; x[3][2] = c.w;
+}
+
+__device__ __forceinline__ void store_tet(int4* v, long long i, const int x[4][3]) {
+  v[3 * i] = make_int4(x[0][0], x[0][1], x[0][2], x[1][0]);
+  v[3 * i + 1] = make_int4(x[1][1], x[1][2], x[2][0], x[2][1]);
+  v[3 * i + 2] = make_int4(x[2][2], x[3][0], x[3][1], x[3][2]);
+}
+
+// Outward face plane of face f (opposite vertex f) as n . p <= rhs with n in
+// {0, +-1}^3: every LEB face is parallel to one of 9 planes.  Returns false if
+// the face normal is not of that form.
+__device__ __forceinline__ bool face_plane(const int x[4][3], int f, int nrm[3], long long* rhs) {
+  const int a = (f + 1) & 3, b = (f + 2) & 3, c = (f + 3) & 3;
+  long long u[3], v[3], w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    u[k] = (long long)x[b][k] - x[a][k];
+    v[k] = (long long)x[c][k] - x[a][k];
+    w[k] = (long long)x[f][k] - x[a][k];
+  }
+  long long n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+  if (n[0] * w[0] + n[1] * w[1] + n[2] * w[2] > 0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+  const long long m = max(max(llabs(n[0]), llabs(n[1])), llabs(n[2]));
+  bool ok = m > 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    nrm[k] = (n[k] > 0) - (n[k] < 0);
+    ok = ok && (n[k] == 0 || llabs(n[k]) == m);
+  }
+  *rhs = (long long)nrm[0] * x[a][0] + (long long)nrm[1] * x[a][1] + (long long)nrm[2] * x[a][2];
+  return ok;
+}
+
+// orientation id (internal encoding p | s << 4) of a canonical outward normal
+__device__ __forceinline__ int orient_id(const int n[3]) {
+  // P = {x, y, z, x+y, x-y, y+z, y-z, x+z, x-z}
+  const int P[9][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0},
+                       {0, 1, 1}, {0, 1, -1}, {1, 0, 1}, {1, 0, -1}};
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    if (n[0] == P[p][0] && n[1] == P[p][1] && n[2] == P[p][2]) return p;
+    if (n[0] == -P[p][0] && n[1] == -P[p][1] && n[2] == -P[p][2]) return p | 16;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int p9_dot(int p, const int v[3]) {
+  switch (p) {
+    case 0: return v[0];
+    case 1: return v[1];
+    case 2: return v[2];
+    case 3: return v[0] + v[1];
+    case 4: return v[0] - v[1];
+    case 5: return v[1] + v[2];
+    case 6: return v[1] - v[2];
+    case 7: return v[0] + v[2];
+    default: return v[0] - v[2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A1: quantise density to q = round(rho 2^24) in [0, 2^24]
+// ---------------------------------------------------------------------------
+__global__ void k_quantize(const float* __restrict__ rho, uint32_t* __restrict__ q, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = rho[i] * 16777216.0f;
+    uint32_t r;
+    if (!(v > 0.0f)) r = 0;
+    else if (v >= 16777216.0f) r = 16777216u;
+    else r = (uint32_t)rintf(v);
+    q[i] = r;
+  }
+}
+
+// A2: six Kuhn tetrahedra per cube, tag 3, in root-id order
+__global__ void k_roots(LeafPtrs L, Geo g, int nroots) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nroots) return;
+  const int perm = r % 6, c = r / 6;
+  const int cube[3] = {c % g.C[0], (c / g.C[0]) % g.C[1], c / (g.C[0] * g.C[1])};
+  const int ax0 = perm < 2 ? 0 : (perm < 4 ? 1 : 2);
+  const int ax1 = (perm == 0 || perm == 5) ? 1 : ((perm == 1 || perm == 3) ? 2 : 0);
+  const int S = 1 << g.K;
+  int x[4][3];
+  for (int a = 0; a < 3; ++a) {
+    x[0][a] = cube[a] * S;
+    x[1][a] = x[0][a] + (a == ax0 ? S : 0);
+    x[2][a] = x[1][a] + (a == ax1 ? S : 0);
+    x[3][a] = x[0][a] + S;
+  }
+  store_tet(L.v, r, x);
+  L.code[r] = (unsigned long long)r << 56;
+  L.tag[r] = 3;
+}
+
+__global__ void k_insert_vertices(const int4* v, long long n, unsigned long long* keys, unsigned long long mask,
+                                  unsigned long long* count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x[4][3];
+  load_tet(v, i, x);
+  for (int k = 0; k < 4; ++k)
+    if (hset_insert(keys, mask, pack3(x[k][0], x[k][1], x[k][2]), count) < 0) atomicAdd(count + 3, 1ull);
+}
+
+__global__ void k_rehash(const unsigned long long* old, long long oldcap, unsigned long long* keys,
+                         unsigned long long mask, unsigned long long* fail) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= oldcap) return;
+  const unsigned long long k = old[i];
+  if (k != EMPTY && hset_insert(keys, mask, k, nullptr) < 0) atomicAdd(fail, 1ull);
+}
+
+// voxel index range of the centres inside [lo, hi] (units of 2^-K) along one axis
+__device__ __forceinline__ void voxel_range(long long lo, long long hi, int h, int dim, int* a, int* b) {
+  // centre (2i + 1) h in [lo, hi]  <=>  (lo - h) / 2h <= i <= (hi - h) / 2h
+  const long long two_h = 2ll * h;
+  long long ilo = lo - h >= 0 ? (lo - h + two_h - 1) / two_h : -((h - lo) / two_h);
+  long long ihi = hi - h >= 0 ? (hi - h) / two_h : -((h - hi + two_h - 1) / two_h);
+  if (ilo < 0) ilo = 0;
+  if (ihi > dim - 1) ihi = dim - 1;
+  *a = (int)ilo;
+  *b = (int)ihi;
+}
+
+__device__ __forceinline__ void tet_box(const int x[4][3], const Geo& g, int lo[3], int hi[3]) {
+  const int dims[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int mn = x[0][a], mx = x[0][a];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) { mn = min(mn, x[k][a]); mx = max(mx, x[k][a]); }
+    voxel_range(mn, mx, g.h, dims[a], &lo[a], &hi[a]);
+  }
+}
+
+// A3 statistics, pass 1: chunk counts of the new leaves; reset their statistics
+__global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo g, unsigned long long* chunks) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const long long i = list ? list[j] : j;
+  int x[4][3], lo[3], hi[3];
+  load_tet(L.v, i, x);
+  tet_box(x, g, lo, hi);
+  long long w = 1;
+  for (int a = 0; a < 3; ++a) w *= (hi[a] >= lo[a]) ? (long long)(hi[a] - lo[a] + 1) : 0;
+  chunks[j] = (unsigned long long)((w + CHUNK - 1) / CHUNK);
+  L.cnt[i] = 0; L.sum[i] = 0; L.mn[i] = 0xFFFFFFFFu; L.mx[i] = 0;
+}
+
+// A3 statistics, pass 2: one warp per chunk of a leaf's voxel box
+__global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long* list, long long m,
+                                                    const unsigned long long* chunk_off, unsigned long long total,
+                                                    const uint32_t* __restrict__ q, Geo g) {
+  const unsigned lane = threadIdx.x & 31u;
+  const long long warps = (long long)gridDim.x * (TPB / 32);
+  for (long long c = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5); c < (long long)total; c += warps) {
+    // leaf j: last chunk_off[j] <= c
+    long long lo_j = 0, hi_j = m;
+    while (lo_j < hi_j) {
+      const long long mid = (lo_j + hi_j) >> 1;
+      if (chunk_off[mid] <= (unsigned long long)c) lo_j = mid + 1; else hi_j = mid;
+    }
+    const long long j = lo_j - 1;
+    const long long i = list ? list[j] : j;
+    int x[4][3], lo[3], hi[3];
+    load_tet(L.v, i, x);
+    tet_box(x, g, lo, hi);
+    int nrm[4][3];
+    long long rhs[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
+    const long long wx = hi[0] - lo[0] + 1, wy = hi[1] - lo[1] + 1, wz = hi[2] - lo[2] + 1;
+    const long long W = wx * wy * wz;
+    const long long start = ((long long)c - (long long)chunk_off[j]) * CHUNK;
+    const long long end = min(start + CHUNK, W);
+    uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
+    unsigned long long sum = 0;
+    for (long long l = start + lane; l < end; l += 32) {
+      const int ii = lo[0] + (int)(l % wx);
+      const int jj = lo[1] + (int)((l / wx) % wy);
+      const int kk = lo[2] + (int)(l / (wx * wy));
+      const long long P[3] = {(2ll * ii + 1) * g.h, (2ll * jj + 1) * g.h, (2ll * kk + 1) * g.h};
+      bool in = true;
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        in = in && (nrm[f][0] * P[0] + nrm[f][1] * P[1] + nrm[f][2] * P[2] <= rhs[f]);
+      if (in) {
+        const uint32_t v = __ldg(q + ((size_t)kk * g.ny + jj) * g.nx + ii);
+        ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      cnt += __shfl_xor_sync(~0u, cnt, o);
+      sum += __shfl_xor_sync(~0u, sum, o);
+      mn = min(mn, __shfl_xor_sync(~0u, mn, o));
+      mx = max(mx, __shfl_xor_sync(~0u, mx, o));
+    }
+    if (lane == 0 && cnt) {
+      atomicAdd(L.cnt + i, cnt);
+      atomicAdd(L.sum + i, sum);
+      atomicMin(L.mn + i, mn);
+      atomicMax(L.mx + i, mx);
+    }
+  }
+}
+
+// Sec. 2 criterion 2 in fp64 with every product and sum rounded on its own.
+__device__ bool camera_allows(const CamD& c, const Geo& g, const int x[4][3]) {
+  if (!c.on) return true;
+  const double s = ldexp(1.0, -g.K);
+  double xc[4], yc[4], zc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double d0 = __dsub_rn(__dmul_rn((double)x[i][0], s), c.eye[0]);
+    const double d1 = __dsub_rn(__dmul_rn((double)x[i][1], s), c.eye[1]);
+    const double d2 = __dsub_rn(__dmul_rn((double)x[i][2], s), c.eye[2]);
+    zc[i] = __dadd_rn(__dadd_rn(__dmul_rn(d0, c.f[0]), __dmul_rn(d1, c.f[1])), __dmul_rn(d2, c.f[2]));
+    xc[i] = __dadd_rn(__dadd_rn(__dmul_rn(d0, c.r[0]), __dmul_rn(d1, c.r[1])), __dmul_rn(d2, c.r[2]));
+    yc[i] = __dadd_rn(__dadd_rn(__dmul_rn(d0, c.u[0]), __dmul_rn(d1, c.u[1])), __dmul_rn(d2, c.u[2]));
+  }
+  bool near_ = true, right = true, left = true, top = true, bottom = true;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double ax = __dmul_rn(zc[i], c.tanX), ay = __dmul_rn(zc[i], c.tanF);
+    near_ = near_ && zc[i] < c.near_g;
+    right = right && xc[i] > ax;
+    left = left && xc[i] < -ax;
+    top = top && yc[i] > ay;
+    bottom = bottom && yc[i] < -ay;
+  }
+  if (near_ || right || left || top || bottom) return false;
+  double zmin = fmin(fmin(zc[0], zc[1]), fmin(zc[2], zc[3]));
+  if (zmin < c.near_g) zmin = c.near_g;
+  long long L2 = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 4; ++j) {
+      long long e = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { const long long t = (long long)x[i][a] - x[j][a]; e += t * t; }
+      L2 = max(L2, e);
+    }
+  const double lmax2 = __dmul_rn(__dmul_rn((double)L2, s), s);
+  const double pix = __dmul_rn(c.thr, zmin);
+  return lmax2 > __dmul_rn(pix, pix);
+}
+
+// A3 statistics, pass 3 (empty D -> voxel of the centroid) and the criterion of every new leaf
+__global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, const uint32_t* __restrict__ q,
+                               Crit C) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const long long i = list ? list[j] : j;
+  int x[4][3];
+  load_tet(L.v, i, x);
+  const Geo& g = C.g;
+  if (L.cnt[i] == 0) {
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    int idx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long s4 = (long long)x[0][a] + x[1][a] + x[2][a] + x[3][a];
+      long long c = s4 >> (g.K + 2 - g.m);
+      idx[a] = (int)(c < 0 ? 0 : (c > dims[a] - 1 ? dims[a] - 1 : c));
+    }
+    const uint32_t v = q[((size_t)idx[2] * g.ny + idx[1]) * g.nx + idx[0]];
+    L.cnt[i] = 1; L.sum[i] = v; L.mn[i] = v; L.mx[i] = v;
+  }
+  const int depth = (int)(L.code[i] & 63ull);
+  bool s = depth < g.max_depth;
+  if (s && C.var_on) {
+    const unsigned __int128 lhs = (unsigned __int128)(L.mx[i] - L.mn[i]) * L.cnt[i] * 65536u;
+    const unsigned __int128 rhs = (unsigned __int128)C.theta_q16 * L.sum[i];
+    s = lhs > rhs;
+  }
+  if (s) s = camera_allows(C.cam, g, x);
+  L.crit[i] = s ? 1 : 0;
+}
+
+// A5: mark = criterion || a vertex of the grid at one of the six edge midpoints
+__global__ void k_mark(LeafPtrs L, long long n, const unsigned long long* keys, unsigned long long mask,
+                       unsigned long long* marks, unsigned long long* nmark) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool mk = false;
+  if (i < n) {
+    mk = L.crit[i] != 0;
+    if (!mk) {
+      int x[4][3];
+      load_tet(L.v, i, x);
+      for (int a = 0; a < 4 && !mk; ++a)
+        for (int b = a + 1; b < 4 && !mk; ++b) {
+          const int s0 = x[a][0] + x[b][0], s1 = x[a][1] + x[b][1], s2 = x[a][2] + x[b][2];
+          if ((s0 | s1 | s2) & 1) continue;        // off the lattice: not a vertex
+          mk = hset_find(keys, mask, pack3(s0 >> 1, s1 >> 1, s2 >> 1)) >= 0;
+        }
+    }
+    marks[i] = mk ? 1 : 0;
+  }
+  const unsigned b = __ballot_sync(~0u, mk);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(nmark, (unsigned long long)__popc(b));
+}
+
+// A4: Maubach bisection of the marked leaves, copy of the others, stable order
+__global__ void k_split(LeafPtrs S, long long n, const unsigned long long* marks, const unsigned long long* pos,
+                        LeafPtrs D, long long* newlist, unsigned long long* keys, unsigned long long mask,
+                        unsigned long long* vcount) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long before = (long long)pos[i];
+  const long long j = i + before;
+  if (!marks[i]) {
+    D.v[3 * j] = S.v[3 * i]; D.v[3 * j + 1] = S.v[3 * i + 1]; D.v[3 * j + 2] = S.v[3 * i + 2];
+    D.code[j] = S.code[i]; D.tag[j] = S.tag[i]; D.crit[j] = S.crit[i];
+    D.cnt[j] = S.cnt[i]; D.sum[j] = S.sum[i]; D.mn[j] = S.mn[i]; D.mx[j] = S.mx[i];
+    return;
+  }
+  int x[4][3];
+  load_tet(S.v, i, x);
+  const int k = S.tag[i];
+  int z[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) z[a] = (x[0][a] + x[k][a]) >> 1;
+  const unsigned long long code = S.code[i];
+  const int depth = (int)(code & 63ull);
+  const unsigned long long base = (code & ~63ull) | (unsigned long long)(depth + 1);
+  const uint8_t nt = (uint8_t)(k > 1 ? k - 1 : 3);
+  for (int w = 0; w < 2; ++w) {
+    int y[4][3];
+    int o = 0;
+    for (int s = w; s < k + w; ++s, ++o)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) y[o][a] = x[s][a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) y[o][a] = z[a];
+    ++o;
+    for (int s = k + 1; s < 4; ++s, ++o)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) y[o][a] = x[s][a];
+    store_tet(D.v, j + w, y);
+    D.code[j + w] = base | ((unsigned long long)w << (55 - depth));
+    D.tag[j + w] = nt;
+    newlist[2 * before + w] = j + w;
+  }
+  if (hset_insert(keys, mask, pack3(z[0], z[1], z[2]), vcount) < 0) atomicAdd(vcount + 3, 1ull);
+}
+
+// A6: face matching
+__device__ __forceinline__ unsigned long long face_key(const int x[4][3], int f) {
+  long long s[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (k != f)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) s[a] += x[k][a];
+  return pack3(s[0], s[1], s[2]);
+}
+
+__global__ void k_face_insert(const int4* v, long long n, unsigned long long* keys, unsigned long long mask,
+                              uint32_t* fcnt, uint32_t* flo, uint32_t* fhi, int* err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x[4][3];
+  load_tet(v, i, x);
+  for (int f = 0; f < 4; ++f) {
+    const long long s = hset_insert(keys, mask, face_key(x, f), nullptr);
+    if (s < 0) { atomicOr(err, 32); return; }
+    const uint32_t id = (uint32_t)(4 * i + f);
+    atomicAdd(fcnt + s, 1u);
+    atomicMin(flo + s, id);
+    atomicMax(fhi + s, id);
+  }
+}
+
+__device__ __forceinline__ bool same_face(const int x[4][3], int f, const int y[4][3], int g) {
+  // the three vertices of face f of x are the three vertices of face g of y
+  for (int a = 0; a < 4; ++a) {
+    if (a == f) continue;
+    bool found = false;
+    for (int b = 0; b < 4; ++b)
+      if (b != g && x[a][0] == y[b][0] && x[a][1] == y[b][1] && x[a][2] == y[b][2]) found = true;
+    if (!found) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t encode_density(double mean, int fmt) {
+  const float f = __double2float_rn(mean);
+  if (fmt == TG_DENSITY_BF16) {
+    const uint32_t u = __float_as_uint(f);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+  }
+  if (fmt == TG_DENSITY_FP16) return (uint32_t)__half_as_ushort(__float2half_rn(f));
+  return __float_as_uint(f);
+}
+
+__global__ void k_finalize(LeafPtrs L, long long n, Geo g, int fmt, const unsigned long long* keys,
+                           unsigned long long mask, const uint32_t* fcnt, const uint32_t* flo, const uint32_t* fhi,
+                           uint4* rec, float* majorant, int* err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x[4][3];
+  load_tet(L.v, i, x);
+  uint32_t link[4];
+  int cpl[4];
+  for (int f = 0; f < 4; ++f) {
+    const long long s = hset_find(keys, mask, face_key(x, f));
+    uint32_t nb = NO_NBR;
+    if (s < 0) { atomicOr(err, 1); return; }
+    const uint32_t c = fcnt[s];
+    const uint32_t me = (uint32_t)(4 * i + f);
+    if (c == 2) {
+      const uint32_t other = flo[s] == me ? fhi[s] : flo[s];
+      int y[4][3];
+      load_tet(L.v, other >> 2, y);
+      if (!same_face(x, f, y, (int)(other & 3))) { atomicOr(err, 2); return; }
+      nb = other >> 2;
+    } else if (c == 1) {
+      // a face of one cell must lie on the domain boundary
+      bool bnd = false;
+      const int a = (f + 1) & 3, b = (f + 2) & 3, cc = (f + 3) & 3;
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const int lim = g.C[ax] << g.K;
+        if (x[a][ax] == x[b][ax] && x[a][ax] == x[cc][ax] && (x[a][ax] == 0 || x[a][ax] == lim)) bnd = true;
+      }
+      if (!bnd) { atomicOr(err, 4); return; }
+    } else {
+      atomicOr(err, 8);
+      return;
+    }
+    int nrm[3];
+    long long rhs;
+    if (!face_plane(x, f, nrm, &rhs)) { atomicOr(err, 16); return; }
+    const int id = orient_id(nrm);
+    if (id < 0) { atomicOr(err, 16); return; }
+    const int v3[3] = {x[(f + 1) & 3][0], x[(f + 1) & 3][1], x[(f + 1) & 3][2]};
+    cpl[f] = p9_dot(id & 15, v3);
+    link[f] = nb | ((uint32_t)id << 27);
+  }
+  const double mean = __ddiv_rn((double)L.sum[i], __dmul_rn((double)L.cnt[i], 16777216.0));
+  const uint32_t m24 = 0xFFFFFFu;
+  rec[2 * i] = make_uint4(link[0], link[1], link[2], link[3]);
+  rec[2 * i + 1] = make_uint4(((uint32_t)cpl[0] & m24) | ((uint32_t)cpl[1] << 24),
+                              (((uint32_t)cpl[1] & m24) >> 8) | ((uint32_t)cpl[2] << 16),
+                              (((uint32_t)cpl[2] & m24) >> 16) | ((uint32_t)cpl[3] << 8), encode_density(mean, fmt));
+  majorant[i] = __double2float_rn(__ddiv_rn((double)L.mx[i], 16777216.0));
+}
+
+__global__ void k_code_depth(const unsigned long long* __restrict__ codes, long long n, int* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(out, (int)(codes[i] & 63ull));
+}
+
+unsigned long long next_pow2(unsigned long long v) {
+  unsigned long long p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+unsigned blocks_for(long long n, int tpb = TPB) { return (unsigned)std::max<long long>(1, (n + tpb - 1) / tpb); }
+
+struct Scanner {
+  DevBuf<char> tmp;
+  void exclusive(const unsigned long long* in, unsigned long long* out, long long n, cudaStream_t st) {
+    size_t bytes = 0;
+    TV_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, st));
+    tmp.ensure(bytes + 16);
+    TV_CUDA(cub::DeviceScan::ExclusiveSum(tmp.p, bytes, in, out, n, st));
+  }
+};
+
+// Statistics and criterion of m new leaves (list == nullptr: leaves 0..m-1).
+void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const uint32_t* q, const Crit& C,
+                         Scanner& scan, DevBuf<unsigned long long>& chunks, DevBuf<unsigned long long>& off,
+                         cudaStream_t st, int sms) {
+  if (m == 0) return;
+  LeafPtrs L = Lv.ptrs();
+  chunks.ensure(m + 1);
+  off.ensure(m + 1);
+  k_stats_prep<<<blocks_for(m), TPB, 0, st>>>(L, list, m, C.g, chunks.p);
+  TV_LAUNCH();
+  TV_CUDA(cudaMemsetAsync(chunks.p + m, 0, sizeof(unsigned long long), st));
+  scan.exclusive(chunks.p, off.p, m + 1, st);
+  unsigned long long total = 0;
+  TV_CUDA(cudaMemcpyAsync(&total, off.p + m, sizeof total, cudaMemcpyDeviceToHost, st));
+  TV_CUDA(cudaStreamSynchronize(st));
+  if (total) {
+    const long long wblocks = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
+    k_stats_scan<<<(unsigned)wblocks, TPB, 0, st>>>(L, list, m, off.p, total, q, C.g);
+    TV_LAUNCH();
+  }
+  k_stats_finish<<<blocks_for(m), TPB, 0, st>>>(L, list, m, q, C);
+  TV_LAUNCH();
+}
+
+void normalize3(double v[3]) {
+  const double l = std::sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+  v[0] /= l; v[1] /= l; v[2] /= l;
+}
+
+void cross3(const double a[3], const double b[3], double r[3]) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Camera of criterion 2 in grid space (host, fp64, each operation rounded on its own).
+CamD camera_for_criterion(const tg_camera* cam, float footprint_px, const float box_min[3], double cube) {
+  CamD c;
+  std::memset(&c, 0, sizeof c);
+  c.on = cam != nullptr && footprint_px > 0.f;
+  if (!c.on) return c;
+  double up[3] = {cam->up[0], cam->up[1], cam->up[2]};
+  for (int a = 0; a < 3; ++a) {
+    c.eye[a] = ((double)cam->pos[a] - (double)box_min[a]) / cube;
+    c.f[a] = (double)cam->target[a] - (double)cam->pos[a];
+  }
+  normalize3(c.f);
+  cross3(c.f, up, c.r);
+  normalize3(c.r);
+  cross3(c.r, c.f, c.u);
+  normalize3(c.u);
+  c.tanF = std::tan((double)cam->fov_y_deg * 0.0087266462599716478846);
+  c.tanX = c.tanF * ((double)cam->width / (double)cam->height);
+  c.near_g = 1e-3 / cube;
+  c.thr = (2.0 * c.tanF / (double)cam->height) * (double)footprint_px;
+  return c;
+}
+
+}  // namespace
+
+int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera* cam, float footprint_px,
+               float theta, int32_t max_depth, int32_t fmt, cudaStream_t st, GridImpl& G) {
+  Geo g;
+  g.nx = vol->nx; g.ny = vol->ny; g.nz = vol->nz;
+  int n = 1, m = 0;
+  while (g.nx % (2 * n) == 0 && g.ny % (2 * n) == 0 && g.nz % (2 * n) == 0 && n < (1 << 18)) { n *= 2; ++m; }
+  g.n = n; g.m = m;
+  g.C[0] = g.nx / n; g.C[1] = g.ny / n; g.C[2] = g.nz / n;
+  g.K = std::max((max_depth + 2) / 3 + 1, m + 1);
+  g.max_depth = max_depth;
+  for (int a = 0; a < 3; ++a)
+    if (((long long)g.C[a] << g.K) > (1ll << 19)) return TG_EINVAL;
+  const int nroots = 6 * g.C[0] * g.C[1] * g.C[2];
+  if (nroots > 256) return TG_EINVAL;
+  g.h = 1 << (g.K - m - 1);
+
+  Crit C;
+  C.g = g;
+  const double cube = (double)vol->voxel_size * (double)n;
+  C.cam = camera_for_criterion(cam, footprint_px, vol->box_min, cube);
+  C.var_on = theta >= 0.f;
+  C.theta_q16 = C.var_on ? (unsigned long long)std::llround((double)theta * 65536.0) : 0ull;
+
+  int dev = 0, sms = 0;
+  TV_CUDA(cudaGetDevice(&dev));
+  TV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+  const long long nvox = (long long)g.nx * g.ny * g.nz;
+  DevBuf<uint32_t> q(nvox);
+  k_quantize<<<(unsigned)std::min<long long>(blocks_for(nvox), (long long)sms * 32), TPB, 0, st>>>(density, q.p, nvox);
+  TV_LAUNCH();
+
+  Leaves A, B;
+  A.ensure(nroots);
+  k_roots<<<blocks_for(nroots), TPB, 0, st>>>(A.ptrs(), g, nroots);
+  TV_LAUNCH();
+
+  // vertex set
+  unsigned long long hcap = next_pow2(std::max<long long>(4096, 8ll * nroots));
+  DevBuf<unsigned long long> hkeys(hcap), counters(4);   // counters: vertices, marks
+  TV_CUDA(cudaMemsetAsync(hkeys.p, 0xFF, hcap * 8, st));
+  TV_CUDA(cudaMemsetAsync(counters.p, 0, 4 * 8, st));
+  k_insert_vertices<<<blocks_for(nroots), TPB, 0, st>>>(A.v.p, nroots, hkeys.p, hcap - 1, counters.p);
+  TV_LAUNCH();
+
+  Scanner scan;
+  DevBuf<unsigned long long> chunks, off, marks, pos;
+  DevBuf<long long> newlist;
+  stats_and_criterion(A, nullptr, nroots, q.p, C, scan, chunks, off, st, sms);
+
+  long long N = nroots;
+  const int max_rounds = 4 * max_depth + 16;
+  int round = 0;
+  for (;; ++round) {
+    marks.ensure(N + 1);
+    pos.ensure(N + 1);
+    TV_CUDA(cudaMemsetAsync(counters.p + 1, 0, 8, st));
+    k_mark<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, hkeys.p, hcap - 1, marks.p, counters.p + 1);
+    TV_LAUNCH();
+    unsigned long long hc[4];
+    TV_CUDA(cudaMemcpyAsync(hc, counters.p, 32, cudaMemcpyDeviceToHost, st));
+    TV_CUDA(cudaStreamSynchronize(st));
+    if (hc[3]) return TG_ENOMEM;                 // the vertex set overflowed
+    const long long M = (long long)hc[1];
+    if (M == 0) break;
+    if (round >= max_rounds) return TG_EROUNDLIMIT;
+    if (N + M > MAX_TETS) return TG_ENOMEM;
+    // grow the vertex set to keep its load under one half
+    if (2 * (hc[0] + (unsigned long long)M) > hcap) {
+      const unsigned long long ncap = next_pow2(4 * (hc[0] + (unsigned long long)M));
+      DevBuf<unsigned long long> nk(ncap);
+      TV_CUDA(cudaMemsetAsync(nk.p, 0xFF, ncap * 8, st));
+      k_rehash<<<blocks_for((long long)hcap), TPB, 0, st>>>(hkeys.p, (long long)hcap, nk.p, ncap - 1,
+                                                            counters.p + 3);
+      TV_LAUNCH();
+      TV_CUDA(cudaStreamSynchronize(st));
+      hkeys = std::move(nk);
+      hcap = ncap;
+    }
+    TV_CUDA(cudaMemsetAsync(marks.p + N, 0, 8, st));
+    scan.exclusive(marks.p, pos.p, N + 1, st);
+    B.ensure(N + M);
+    newlist.ensure(2 * M);
+    k_split<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, marks.p, pos.p, B.ptrs(), newlist.p, hkeys.p, hcap - 1,
+                                           counters.p);
+    TV_LAUNCH();
+    std::swap(A, B);
+    N += M;
+    stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, st, sms);
+  }
+
+  // ---- finalize: neighbours, orientations, planes, densities, records ----
+  const unsigned long long fcap = next_pow2(std::max<long long>(1024, 4 * N));
+  DevBuf<unsigned long long> fkeys(fcap);
+  DevBuf<uint32_t> fcnt(fcap), flo(fcap), fhi(fcap);
+  TV_CUDA(cudaMemsetAsync(fkeys.p, 0xFF, fcap * 8, st));
+  TV_CUDA(cudaMemsetAsync(fcnt.p, 0, fcap * 4, st));
+  TV_CUDA(cudaMemsetAsync(flo.p, 0xFF, fcap * 4, st));
+  TV_CUDA(cudaMemsetAsync(fhi.p, 0, fcap * 4, st));
+  DevBuf<uint4> rec(2 * N);
+  DevBuf<float> maj(N);
+  DevBuf<int> err(2);
+  TV_CUDA(cudaMemsetAsync(err.p, 0, 8, st));
+  k_face_insert<<<blocks_for(N), TPB, 0, st>>>(A.v.p, N, fkeys.p, fcap - 1, fcnt.p, flo.p, fhi.p, err.p);
+  TV_LAUNCH();
+  k_finalize<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, g, fmt, fkeys.p, fcap - 1, fcnt.p, flo.p, fhi.p, rec.p,
+                                            maj.p, err.p);
+  TV_LAUNCH();
+  int herr = 0;
+  TV_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
+  TV_CUDA(cudaStreamSynchronize(st));
+  if (herr) return TG_EGRID;
+
+  // exact-size copies of the arrays the grid keeps
+  DevBuf<unsigned long long> codes(N), sum(N), scratch(4);
+  DevBuf<int4> verts(3 * N);
+  DevBuf<uint8_t> tag(N);
+  DevBuf<uint32_t> cnt(N), mn(N), mx(N);
+  TV_CUDA(cudaMemcpyAsync(codes.p, A.code.p, N * 8, cudaMemcpyDeviceToDevice, st));
+  TV_CUDA(cudaMemcpyAsync(sum.p, A.sum.p, N * 8, cudaMemcpyDeviceToDevice, st));
+  TV_CUDA(cudaMemcpyAsync(verts.p, A.v.p, N * 48, cudaMemcpyDeviceToDevice, st));
+  TV_CUDA(cudaMemcpyAsync(tag.p, A.tag.p, N, cudaMemcpyDeviceToDevice, st));
+  TV_CUDA(cudaMemcpyAsync(cnt.p, A.cnt.p, N * 4, cudaMemcpyDeviceToDevice, st));
+  TV_CUDA(cudaMemcpyAsync(mn.p, A.mn.p, N * 4, cudaMemcpyDeviceToDevice, st));
+  TV_CUDA(cudaMemcpyAsync(mx.p, A.mx.p, N * 4, cudaMemcpyDeviceToDevice, st));
+  TV_CUDA(cudaMemsetAsync(scratch.p, 0, 32, st));
+  int depth_reached = 0;
+  TV_CUDA(cudaMemsetAsync(err.p + 1, 0, 4, st));
+  k_code_depth<<<blocks_for(N), TPB, 0, st>>>(codes.p, N, err.p + 1);
+  TV_LAUNCH();
+  TV_CUDA(cudaMemcpyAsync(&depth_reached, err.p + 1, 4, cudaMemcpyDeviceToHost, st));
+  TV_CUDA(cudaStreamSynchronize(st));
+
+  G.device = dev;
+  G.n = N;
+  G.K = g.K;
+  G.max_depth = depth_reached;
+  G.rounds = round;
+  G.fmt = fmt;
+  for (int a = 0; a < 3; ++a) { G.C[a] = g.C[a]; G.box_min[a] = vol->box_min[a]; }
+  G.nvox[0] = g.nx; G.nvox[1] = g.ny; G.nvox[2] = g.nz;
+  G.n_per_cube = n;
+  G.voxel_size = vol->voxel_size;
+  G.cube = cube;
+  G.rec = rec.release();
+  G.majorant = maj.release();
+  G.codes = codes.release();
+  G.sum = sum.release();
+  G.verts = reinterpret_cast<int32_t*>(verts.release());
+  G.tag = tag.release();
+  G.count = cnt.release();
+  G.qmin = mn.release();
+  G.qmax = mx.release();
+  G.scratch = scratch.release();
+  return TG_OK;
+}
+
+}  // namespace tv
+
+extern "C" int leb_build(const float* density, const tg_volume_desc* vol, const tg_camera* cam,
+                         float target_footprint_px, float variation_threshold, int32_t max_depth,
+                         int32_t density_format, void* cuda_stream, tg_grid** out) {
+  if (!density || !vol || !out || vol->nx <= 0 || vol->ny <= 0 || vol->nz <= 0 || !(vol->voxel_size > 0) ||
+      max_depth < 0 || max_depth > 50 || density_format < 0 || density_format > 2)
+    return TG_EINVAL;
+  if ((long long)vol->nx * vol->ny * vol->nz >= (1ll << 34)) return TG_EINVAL;
+  if (cam && !tv::camera_ok(cam)) return TG_EINVAL;
+  tg_grid* g = new (std::nothrow) tg_grid();
+  if (!g) return TG_ENOMEM;
+  int st;
+  try {
+    st = tv::build_grid(density, vol, cam, target_footprint_px, variation_threshold, max_depth, density_format,
+                        (cudaStream_t)cuda_stream, g->impl);
+  } catch (const tv::Error& e) {
+    st = e.code;
+  } catch (const std::bad_alloc&) {
+    st = TG_ENOMEM;
+  }
+  if (st != TG_OK) {
+    delete g;
+    return st;
+  }
+  *out = g;
+  return TG_OK;
+}

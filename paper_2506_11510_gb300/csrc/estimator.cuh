@@ -1,0 +1,305 @@
+// The path estimator of Sec. 3 (Algorithm 1 plus sun next-event estimation) as
+// one persistent kernel over a cell walker.  Every warp keeps 32 paths in
+// flight; a lane whose path ends takes a new path id from a global counter
+// (one atomic per warp, ballot + popc to hand out the ids), so lanes keep
+// walking while the warp's other paths finish (warp-level regeneration).
+//
+// Precision.  Where a free flight ends depends on the optical depth consumed
+// along it; a flight that starts in dense medium and ends in thin medium turns
+// an error dx at its start into sigma_start / sigma_end * dx at its end, and
+// these ratios multiply over the bounces of a path.  So the quantities that
+// place the collisions are kept above fp32 precision, cheaply:
+//  * camera rays are formed in fp64 once per path (the eye is far from the
+//    medium, so a direction error becomes a large transverse offset) and kept
+//    as float-float pairs;
+//  * segment origins (collision points) and the optical depth still to
+//    consume are float-float (about 44 bits, on the FP32 pipe);
+//  * the per-segment plane terms P[p] . o are float-float, so exit parameters
+//    carry an error relative to the distance walked, not to |o|.
+// Exit parameters, directions after scattering, densities and shadow walks are
+// fp32: their errors are not amplified.  GB300's FP64 rate is far too low for
+// the per-cell loop; shadow walks are the majority of all cell steps.
+//
+// Walker interface (tetrahedra: walk_tet.cuh, voxels: walk_voxel.cuh):
+//   bool intersect(o, d, &t_in)   slab test with the domain box (fp32)
+//   bool locate(p)                current cell := the cell that holds p
+//   void begin_free(o, d)         per-segment tables for the free flight o + t d
+//   Hop  hop_free(t)              exit parameter of the current cell
+//   void begin_shadow(o, w)       fp32 tables for the shadow ray towards w
+//   Hop  hop_shadow(t)            fp32 exit parameter of the current cell
+//   bool advance()                move to the pending cell (false: boundary)
+//   int  save() / restore(c)      remember / return to a cell
+//   int  cell()                   current cell id (for traces)
+#pragma once
+#include "common.cuh"
+
+namespace tv {
+
+constexpr int EST_BLOCK = 256;
+constexpr int SEG_STEP_LIMIT = 1 << 20;      // cells per segment before a walk gives up
+// A shadow walk whose optical depth passes this value contributes at most
+// E * beta * p * e^-40 < 1e-16 and is stopped early (not in trace mode).
+constexpr float SHADOW_TAU_CUTOFF = 40.0f;
+
+enum : int { S_IDLE = 0, S_FREE = 1, S_SHADOW = 2, S_DONE = 3 };
+
+struct Hop {
+  float texit;
+  float rho;
+  bool ok;
+};
+
+struct EstParams {
+  CamF cam;
+  MedF med;
+  uint64_t seed;
+  int spp, sample_offset;
+  long long total;                          // number of paths
+  unsigned long long* counter;              // path-id counter, zero at launch
+  float* sum;
+  float* sumsq;
+  tg_stats* stats;
+  int regen_min;                            // idle lanes needed before a warp refills
+  // trace mode (per-path outputs for a list of paths)
+  const int32_t *px, *py, *ps;
+  float* outL;
+  int32_t *outFlags, *outColl;
+  int64_t* outSteps;
+  int32_t* seq;
+  int32_t seq_cap;
+  int32_t* seq_len;
+};
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
+  return v;
+}
+
+// IntersectGrid (Sec. 3): slab test of the ray with the domain box [0, C] in grid space.
+__device__ __forceinline__ bool box_intersect(const int C[3], float3 o, float3 d, float* t_in) {
+  float tn = 0.f, tf = INFINITY;
+  const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float hi = (float)C[a];
+    if (dd[a] == 0.f) {
+      if (oo[a] < 0.f || oo[a] > hi) return false;
+      continue;
+    }
+    const float t1 = (0.f - oo[a]) / dd[a], t2 = (hi - oo[a]) / dd[a];
+    tn = fmaxf(tn, fminf(t1, t2));
+    tf = fminf(tf, fmaxf(t1, t2));
+  }
+  *t_in = tn;
+  return tn < tf;
+}
+
+template <class Walker, bool TRACE>
+__global__ void __launch_bounds__(EST_BLOCK) k_estimate(const typename Walker::Params wp, const EstParams ep) {
+  extern __shared__ double smem_d[];
+  Walker W(wp, smem_d);
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt = (1u << lane) - 1u;
+  const MedF& M = ep.med;
+
+  int state = S_IDLE;
+  long long pid = 0;
+  uint32_t pixel = 0, sample = 0;
+  ff3 o = {ff_make(0.f), ff_make(0.f), ff_make(0.f)};   // segment origin
+  ff3 d = o;                                           // path direction (float-float on camera rays)
+  float t = 0.f;                                       // free flight: parameter
+  ff tau = ff_make(0.f);                               // free flight: optical depth left
+  float ts = 0.f, od = 0.f;                            // shadow walk: parameter, optical depth so far
+  float beta = 1.f;
+  ff L = ff_make(0.f);
+  const ff sig_unit = ff{M.sig_hi, M.sig_lo};
+  int bounce = 0, seg_steps = 0, flags = 0, ncoll = 0, saved = 0, seqn = 0;
+  long long psteps = 0;
+  unsigned long long c_paths = 0, c_steps = 0, c_shadow = 0, c_coll = 0, c_esc = 0, c_trunc = 0, c_lim = 0,
+                     c_miss = 0;
+
+  auto record = [&](int v) {
+    if (TRACE) {
+      if (seqn < ep.seq_cap) ep.seq[pid * ep.seq_cap + seqn] = v;
+      ++seqn;
+    }
+  };
+  auto finish = [&]() {
+    ++c_paths;
+    if (TRACE) {
+      if (ep.outL) ep.outL[pid] = ff_float(L);
+      if (ep.outFlags) ep.outFlags[pid] = flags;
+      if (ep.outColl) ep.outColl[pid] = ncoll;
+      if (ep.outSteps) ep.outSteps[pid] = psteps;
+      if (ep.seq_len) ep.seq_len[pid] = seqn < ep.seq_cap ? seqn : ep.seq_cap;
+    } else {
+      const float Lf = ff_float(L);
+      atomicAdd(ep.sum + pixel, Lf);
+      if (ep.sumsq) atomicAdd(ep.sumsq + pixel, Lf * Lf);
+    }
+    state = S_IDLE;
+  };
+  auto new_flight = [&](int b) {
+    t = 0.f;
+    tau = ff_make(-logf(1.0f - rng_u(ep.seed, pixel, sample, 2 + 3 * b)));   // SampleFreePath
+    seg_steps = 0;
+    W.begin_free(o, d);
+    state = S_FREE;
+  };
+
+  for (;;) {
+    // ---- regeneration: idle lanes of the warp take consecutive path ids ----
+    const unsigned idle = __ballot_sync(~0u, state == S_IDLE);
+    const unsigned busy = __ballot_sync(~0u, state == S_FREE || state == S_SHADOW);
+    if (idle && (busy == 0 || __popc(idle) >= ep.regen_min)) {
+      const int leader = __ffs(idle) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(ep.counter, (unsigned long long)__popc(idle));
+      base = __shfl_sync(~0u, base, leader);
+      if (state == S_IDLE) {
+        pid = (long long)(base + __popc(idle & lt));
+        if (pid >= ep.total) {
+          state = S_DONE;
+        } else {
+          // ---- a new path: camera ray, IntersectGrid, GridIntersectionPoint ----
+          int px, py, s;
+          if (TRACE) {
+            px = ep.px[pid]; py = ep.py[pid]; s = ep.ps[pid];
+          } else {
+            const long long pix = pid / ep.spp;
+            s = ep.sample_offset + (int)(pid - pix * ep.spp);
+            px = (int)(pix % ep.cam.W);
+            py = (int)(pix / ep.cam.W);
+          }
+          pixel = (uint32_t)(py * ep.cam.W + px);
+          sample = (uint32_t)s;
+          flags = 0; ncoll = 0; psteps = 0; seqn = 0; L = ff_make(0.f); beta = 1.f; bounce = 0;
+          const double u0 = rng_u(ep.seed, pixel, sample, 0), u1 = rng_u(ep.seed, pixel, sample, 1);
+          const CamF& c = ep.cam;
+          const double sx = (2.0 * (((double)px + u0) / (double)c.W) - 1.0) * c.tanF * c.aspect;
+          const double sy = (2.0 * (((double)py + u1) / (double)c.H) - 1.0) * c.tanF;
+          double dx = c.fwd[0] + sx * c.right[0] - sy * c.up[0];
+          double dy = c.fwd[1] + sx * c.right[1] - sy * c.up[1];
+          double dz = c.fwd[2] + sx * c.right[2] - sy * c.up[2];
+          const double inv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+          dx *= inv; dy *= inv; dz *= inv;
+          d = ff3{ff{(float)dx, (float)(dx - (double)(float)dx)}, ff{(float)dy, (float)(dy - (double)(float)dy)},
+                  ff{(float)dz, (float)(dz - (double)(float)dz)}};
+          const float3 dir = make_float3(d.x.hi, d.y.hi, d.z.hi);
+          const float3 eye = make_float3((float)c.eye[0], (float)c.eye[1], (float)c.eye[2]);
+          float tin;
+          if (!W.intersect(eye, dir, &tin)) {
+            L = ff_make(M.Lenv); flags = 4; ++c_miss; ++c_esc;
+            finish();
+          } else {
+            // the entry point: any error along the ray is harmless (no medium outside the box)
+            o = ff3{ff_add(ff{(float)c.eye[0], (float)(c.eye[0] - (double)(float)c.eye[0])}, ff_mul_f(d.x, tin)),
+                    ff_add(ff{(float)c.eye[1], (float)(c.eye[1] - (double)(float)c.eye[1])}, ff_mul_f(d.y, tin)),
+                    ff_add(ff{(float)c.eye[2], (float)(c.eye[2] - (double)(float)c.eye[2])}, ff_mul_f(d.z, tin))};
+            if (!W.locate(make_float3(ff_float(o.x), ff_float(o.y), ff_float(o.z)))) {
+              flags = 16;
+              finish();
+            } else {
+              new_flight(0);
+            }
+          }
+        }
+      }
+    }
+    if (__all_sync(~0u, state == S_DONE)) break;
+    if (state != S_FREE && state != S_SHADOW) continue;
+
+    record(W.cell());
+    ++seg_steps; ++psteps;
+    if (state == S_FREE) {
+      // ---- one cell of MarchThroughCells: ReadDensity, consume the free path ----
+      ++c_steps;
+      const Hop h = W.hop_free(t);
+      if (!h.ok) { flags |= 16; finish(); continue; }
+      const ff sig = ff_mul_f(sig_unit, h.rho);
+      const ff dtau = ff_mul_f(sig, h.texit - t);
+      if (h.rho > 0.f && !ff_lt(dtau, tau)) {
+        // collision: albedo weight, then next-event estimation towards the sun
+        const ff tc = ff_add(ff_make(t), ff_div(tau, sig));
+        o = ff3{ff_add(o.x, ff_mul(tc, d.x)), ff_add(o.y, ff_mul(tc, d.y)), ff_add(o.z, ff_mul(tc, d.z))};
+        beta *= M.albedo;
+        ++ncoll; ++c_coll;
+        record(-1);
+        saved = W.save();
+        W.begin_shadow(o, make_float3(M.sun_w[0], M.sun_w[1], M.sun_w[2]));
+        ts = 0.f; od = 0.f; seg_steps = 0;
+        state = S_SHADOW;
+        continue;
+      }
+      tau = ff_sub(tau, dtau);
+      t = h.texit;
+      if (!W.advance()) {
+        L = ff_add(L, ff_make(beta * M.Lenv)); ++c_esc;
+        finish();
+        continue;
+      }
+    } else {
+      // ---- one cell of the shadow walk (transmittance to the boundary) ----
+      ++c_shadow;
+      const Hop h = W.hop_shadow(ts);
+      if (!h.ok) { flags |= 16; finish(); continue; }
+      od += M.sig_hi * h.rho * (h.texit - ts);
+      ts = h.texit;
+      const bool out = !W.advance();
+      if (out || (!TRACE && od > SHADOW_TAU_CUTOFF)) {
+        record(-1);
+        const float tr = out ? expf(-od) : 0.0f;
+        const float cs = d.x.hi * M.sun_w[0] + d.y.hi * M.sun_w[1] + d.z.hi * M.sun_w[2];
+        L = ff_add(L, ff_make(beta * hg_eval(M.g, cs) * M.E * tr));
+        if (bounce + 1 >= M.max_bounces) {
+          flags |= 2; ++c_trunc;
+          finish();
+          continue;
+        }
+        // SamplePhaseFunction, then a new free flight from the collision point
+        const float3 nd = hg_scatter(M.g, rng_u(ep.seed, pixel, sample, 3 + 3 * bounce),
+                                     rng_u(ep.seed, pixel, sample, 4 + 3 * bounce),
+                                     make_float3(d.x.hi, d.y.hi, d.z.hi));
+        d = ff3{ff_make(nd.x), ff_make(nd.y), ff_make(nd.z)};
+        ++bounce;
+        W.restore(saved);
+        new_flight(bounce);
+        continue;
+      }
+    }
+    if (seg_steps >= SEG_STEP_LIMIT) {
+      flags |= 8; ++c_lim;
+      finish();
+    }
+  }
+
+  if (ep.stats) {
+    const unsigned long long v[8] = {warp_sum(c_paths), warp_sum(c_steps), warp_sum(c_shadow), warp_sum(c_coll),
+                                     warp_sum(c_esc), warp_sum(c_trunc), warp_sum(c_lim), warp_sum(c_miss)};
+    if (lane == 0) {
+      unsigned long long* s = reinterpret_cast<unsigned long long*>(ep.stats);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (v[i]) atomicAdd(s + i, v[i]);
+    }
+  }
+}
+
+// Launch the persistent estimator: as many resident blocks as fit, one wave.
+template <class Walker, bool TRACE>
+void launch_estimate(const typename Walker::Params& wp, const EstParams& ep, cudaStream_t st) {
+  int dev = 0, sms = 0, per_sm = 0;
+  TV_CUDA(cudaGetDevice(&dev));
+  TV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t shm = Walker::smem_bytes();
+  TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<Walker, TRACE>, EST_BLOCK, shm));
+  if (per_sm < 1) per_sm = 1;
+  long long blocks = (long long)sms * per_sm;
+  const long long need = (ep.total + EST_BLOCK - 1) / EST_BLOCK;
+  if (blocks > need) blocks = need < 1 ? 1 : need;
+  k_estimate<Walker, TRACE><<<(unsigned)blocks, EST_BLOCK, shm, st>>>(wp, ep);
+  TV_LAUNCH();
+}
+
+}  // namespace tv

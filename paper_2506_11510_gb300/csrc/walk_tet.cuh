@@ -1,0 +1,257 @@
+// Cell walker over the tetrahedral grid (Sec. 3, "Path Tracing within
+// Tetrahedral Grids"): the exit face of the current cell is found among the
+// faces whose stored orientation faces along the ray (at most three), and the
+// ray moves to the neighbour across it.
+//
+// Face planes only take the 9 orientations P = {x, y, z, x+y, x-y, y+z, y-z,
+// x+z, x-z}, so per segment the walker keeps, for each orientation p,
+// nO[p] = (P[p] . o) 2^K and invND[p] = 2^-K / (P[p] . d) in shared memory
+// (one column per thread: conflict-free), and the exit parameter of a face with
+// integer plane offset c (units of 2^-K) is (c - nO[p]) * invND[p].  A 32-bit
+// mask marks the orientation ids p | s << 4 whose outward normal points along d.
+// Free flights keep nO as a float-float pair (hi, lo), so that c - nO is
+// accurate to the distance walked rather than to |o|; shadow walks keep it as
+// one float.  Both use the same per-thread 8-byte slots.
+#pragma once
+#include "estimator.cuh"
+
+namespace tv {
+
+struct TetParams {
+  const uint4* rec;
+  const unsigned long long* codes;
+  long long n;
+  int K, depth;                 // vertex scale exponent; deepest level present
+  int C[3];                     // cubes per axis
+  float scaleK, invK;           // 2^K, 2^-K
+};
+
+__device__ __forceinline__ int sext24(uint32_t v) { return ((int)(v << 8)) >> 8; }
+
+template <int FMT>
+__device__ __forceinline__ float decode_density(uint32_t w) {
+  if (FMT == TG_DENSITY_BF16) return __uint_as_float(w << 16);
+  if (FMT == TG_DENSITY_FP16) return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
+  return __uint_as_float(w);
+}
+
+// Point location by descent of the LEB hierarchy: from the Kuhn root holding
+// p, take at every bisection the child on p's side of the cutting plane (the
+// child holding x0 when p lies on it) down to the deepest level of the grid;
+// the cell is then the last code <= the point's code (depth-first order).
+inline __device__ long long tet_locate(const TetParams& P, float3 p) {
+  const float pc[3] = {p.x, p.y, p.z};
+  int cube[3];
+  float fr[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int c = (int)floorf(pc[a]);
+    c = c < 0 ? 0 : (c > P.C[a] - 1 ? P.C[a] - 1 : c);
+    cube[a] = c;
+    fr[a] = pc[a] - (float)c;
+  }
+  // Kuhn permutation (a, b, c) holds fr[a] >= fr[b] >= fr[c]; permutations in lexicographic order
+  int perm;
+  if (fr[0] >= fr[1] && fr[1] >= fr[2]) perm = 0;
+  else if (fr[0] >= fr[2] && fr[2] >= fr[1]) perm = 1;
+  else if (fr[1] >= fr[0] && fr[0] >= fr[2]) perm = 2;
+  else if (fr[1] >= fr[2] && fr[2] >= fr[0]) perm = 3;
+  else if (fr[2] >= fr[0] && fr[0] >= fr[1]) perm = 4;
+  else perm = 5;
+  const int ax0 = (perm < 2) ? 0 : (perm < 4 ? 1 : 2);
+  const int ax1 = (perm == 0 || perm == 5) ? 1 : ((perm == 1 || perm == 3) ? 2 : 0);
+  const int S = 1 << P.K;
+  int x[4][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    x[0][a] = cube[a] * S;
+    x[1][a] = x[0][a] + (a == ax0 ? S : 0);
+    x[2][a] = x[1][a] + (a == ax1 ? S : 0);
+    x[3][a] = x[0][a] + S;
+  }
+  const unsigned long long root = (unsigned long long)(((cube[2] * P.C[1] + cube[1]) * P.C[0] + cube[0]) * 6 + perm);
+  int k = 3;
+  unsigned long long path = 0;
+  for (int lev = 0; lev < P.depth; ++lev) {
+    int z2[3], u[3], v[3];
+    const int ia = k == 1 ? 2 : 1;       // the two vertices other than x0 and xk
+    const int ib = k == 3 ? 2 : 3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      z2[a] = x[0][a] + x[k][a];
+      u[a] = 2 * x[ia][a] - z2[a];
+      v[a] = 2 * x[ib][a] - z2[a];
+    }
+    const long long n0 = (long long)u[1] * v[2] - (long long)u[2] * v[1];
+    const long long n1 = (long long)u[2] * v[0] - (long long)u[0] * v[2];
+    const long long n2 = (long long)u[0] * v[1] - (long long)u[1] * v[0];
+    const int c0 = (n0 > 0) - (n0 < 0), c1 = (n1 > 0) - (n1 < 0), c2 = (n2 > 0) - (n2 < 0);
+    const long long s0 = (long long)c0 * (2 * x[0][0] - z2[0]) + (long long)c1 * (2 * x[0][1] - z2[1]) +
+                         (long long)c2 * (2 * x[0][2] - z2[2]);
+    const float cp = (float)c0 * p.x + (float)c1 * p.y + (float)c2 * p.z;
+    const float cz = (float)(c0 * z2[0] + c1 * z2[1] + c2 * z2[2]) * (0.5f * P.invK);
+    const int side = (cp == cz || ((cp > cz) == (s0 > 0))) ? 0 : 1;
+    path = (path << 1) | (unsigned long long)side;
+    int y[4][3];
+    int j = 0;
+    if (side == 0) {
+      for (int i = 0; i < k; ++i, ++j)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) y[j][a] = x[i][a];
+    } else {
+      for (int i = 1; i <= k; ++i, ++j)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) y[j][a] = x[i][a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) y[j][a] = z2[a] >> 1;
+    ++j;
+    for (int i = k + 1; i < 4; ++i, ++j)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) y[j][a] = x[i][a];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) x[i][a] = y[i][a];
+    k = k > 1 ? k - 1 : 3;
+  }
+  const unsigned long long bits = P.depth ? ((path << (56 - P.depth)) & ((1ull << 56) - 1)) : 0ull;
+  const unsigned long long key = (root << 56) | bits | (unsigned long long)P.depth;
+  // last code <= key
+  long long lo = 0, hi = P.n;          // invariant: codes[lo-1] <= key < codes[hi]
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if (P.codes[mid] <= key) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+template <int FMT>
+struct TetWalker {
+  using Params = TetParams;
+  const TetParams& P;
+  double* tab;         // this thread's column: slot q at tab[q * EST_BLOCK], 18 slots
+  uint32_t mask;
+  int cur, nxt;
+
+  static size_t smem_bytes() { return sizeof(double) * 18 * EST_BLOCK; }
+
+  __device__ TetWalker(const TetParams& p, double* smem) : P(p), tab(smem + threadIdx.x), mask(0), cur(0), nxt(0) {}
+
+  __device__ __forceinline__ float& ftab(int q) { return *reinterpret_cast<float*>(tab + q * EST_BLOCK); }
+  __device__ __forceinline__ float ftab(int q) const { return *reinterpret_cast<const float*>(tab + q * EST_BLOCK); }
+
+  __device__ __forceinline__ float2& pair(int q) { return *reinterpret_cast<float2*>(tab + q * EST_BLOCK); }
+  __device__ __forceinline__ ff pair_ff(int q) const {
+    const float2 v = *reinterpret_cast<const float2*>(tab + q * EST_BLOCK);
+    return ff{v.x, v.y};
+  }
+
+  __device__ bool intersect(float3 o, float3 d, float* t_in) const { return box_intersect(P.C, o, d, t_in); }
+
+  __device__ bool locate(float3 p) {
+    const long long c = tet_locate(P, p);
+    cur = (int)c;
+    return c >= 0;
+  }
+
+  // nO[p] = (P[p] . o) 2^K as a float-float pair, invND[p] = 2^-K / (P[p] . d) as a float
+  __device__ void begin_free(const ff3& o, const ff3& d) {
+    const ff no[9] = {o.x, o.y, o.z, ff_add(o.x, o.y), ff_sub(o.x, o.y), ff_add(o.y, o.z), ff_sub(o.y, o.z),
+                      ff_add(o.x, o.z), ff_sub(o.x, o.z)};
+    const float nd[9] = {ff_float(d.x), ff_float(d.y), ff_float(d.z), ff_float(ff_add(d.x, d.y)),
+                         ff_float(ff_sub(d.x, d.y)), ff_float(ff_add(d.y, d.z)), ff_float(ff_sub(d.y, d.z)),
+                         ff_float(ff_add(d.x, d.z)), ff_float(ff_sub(d.x, d.z))};
+    uint32_t m = 0;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      pair(p) = make_float2(no[p].hi * P.scaleK, no[p].lo * P.scaleK);
+      ftab(9 + p) = __fdiv_rn(P.invK, nd[p]);
+      m |= (nd[p] > 0.f ? 1u : 0u) << p;
+      m |= (nd[p] < 0.f ? 1u : 0u) << (p + 16);
+    }
+    mask = m;
+  }
+
+  __device__ void begin_shadow(const ff3& o, float3 w) {
+    const ff no[9] = {o.x, o.y, o.z, ff_add(o.x, o.y), ff_sub(o.x, o.y), ff_add(o.y, o.z), ff_sub(o.y, o.z),
+                      ff_add(o.x, o.z), ff_sub(o.x, o.z)};
+    const float nd[9] = {w.x, w.y, w.z, w.x + w.y, w.x - w.y, w.y + w.z, w.y - w.z, w.x + w.z, w.x - w.z};
+    uint32_t m = 0;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      ftab(p) = ff_float(no[p]) * P.scaleK;
+      ftab(9 + p) = __fdiv_rn(P.invK, nd[p]);
+      m |= (nd[p] > 0.f ? 1u : 0u) << p;
+      m |= (nd[p] < 0.f ? 1u : 0u) << (p + 16);
+    }
+    mask = m;
+  }
+
+  __device__ __forceinline__ void load(uint4& a, uint4& b) const {
+    a = __ldg(P.rec + 2 * (size_t)cur);
+    b = __ldg(P.rec + 2 * (size_t)cur + 1);
+  }
+
+  __device__ __forceinline__ Hop hop_free(float t) {
+    uint4 a, b;
+    load(a, b);
+    const uint32_t link[4] = {a.x, a.y, a.z, a.w};
+    const int c[4] = {sext24(b.x), sext24((b.x >> 24) | (b.y << 8)), sext24((b.y >> 16) | (b.z << 16)),
+                      sext24(b.z >> 8)};
+    float best = INFINITY;
+    uint32_t blink = NO_NBR;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const uint32_t id = link[f] >> 27;
+      if ((mask >> id) & 1u) {
+        const int p = (int)(id & 15u);
+        const float2 no = *reinterpret_cast<const float2*>(tab + p * EST_BLOCK);
+        const float tf = __fsub_rn(__fsub_rn((float)c[f], no.x), no.y) * ftab(9 + p);
+        if (tf < best) { best = tf; blink = link[f]; }
+      }
+    }
+    nxt = (int)(blink & NO_NBR);
+    Hop h;
+    h.ok = best < INFINITY;
+    h.texit = fmaxf(best, t);
+    h.rho = decode_density<FMT>(b.w);
+    return h;
+  }
+
+  __device__ __forceinline__ Hop hop_shadow(float t) {
+    uint4 a, b;
+    load(a, b);
+    const uint32_t link[4] = {a.x, a.y, a.z, a.w};
+    const int c[4] = {sext24(b.x), sext24((b.x >> 24) | (b.y << 8)), sext24((b.y >> 16) | (b.z << 16)),
+                      sext24(b.z >> 8)};
+    float best = INFINITY;
+    uint32_t blink = NO_NBR;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const uint32_t id = link[f] >> 27;
+      if ((mask >> id) & 1u) {
+        const int p = (int)(id & 15u);
+        const float tf = ((float)c[f] - ftab(p)) * ftab(9 + p);
+        if (tf < best) { best = tf; blink = link[f]; }
+      }
+    }
+    nxt = (int)(blink & NO_NBR);
+    Hop h;
+    h.ok = best < INFINITY;
+    h.texit = fmaxf(best, t);
+    h.rho = decode_density<FMT>(b.w);
+    return h;
+  }
+
+  __device__ __forceinline__ bool advance() {
+    if ((uint32_t)nxt == NO_NBR) return false;
+    cur = nxt;
+    return true;
+  }
+  __device__ __forceinline__ int save() const { return cur; }
+  __device__ __forceinline__ void restore(int c) { cur = c; }
+  __device__ __forceinline__ int cell() const { return cur; }
+};
+
+}  // namespace tv

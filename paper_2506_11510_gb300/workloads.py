@@ -191,7 +191,7 @@ SCENES = {
         box_min=(0.0, 0.0, 0.0), voxel_size=1.0 / 512,
         camera=Camera((1.0, 1.0, -2.6), (1.0, 1.0, 0.5), (0.0, 1.0, 0.0), 45.0, 1024, 1024),
         medium=Medium(0.95, 0.7, 64.0, 128, _norm((-1.0, -1.0, 1.0)), 3.0, 0.25),
-        spp=32, render_seed=9, footprint_px=1.0, variation_threshold=0.5,
+        spp=32, render_seed=9, footprint_px=1.0, variation_threshold=2.0,
         max_depth=30, density_format=1),
 }
 

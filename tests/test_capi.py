@@ -1,0 +1,56 @@
+"""The C-ABI library loads on any machine (no GPU needed) and exports every
+entry point that include/tetvol.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tetvol.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "sizeof")))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("leb_build", "tet_render", "grid_render", "tg_grid_export", "tg_grid_info", "tg_grid_free",
+              "tg_error_string", "tet_trace_paths", "tet_optical_depth", "tg_grid_import", "grid_trace_paths"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2506_11510_gb300 import _build, _native
+    _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    for n in declared_functions():
+        assert hasattr(lib, n), "libtetvol.so does not export %s" % n
+    assert set(_native.SIGNATURES) == set(declared_functions())
+
+
+def test_error_strings_without_a_gpu():
+    from paper_2506_11510_gb300 import _native as N
+    L = N.lib()
+    assert L.tg_error_string(0) == b"ok"
+    assert L.tg_error_string(-6) == b"grid is not conforming"
+    assert L.tg_error_string(12345) == b"unknown status"
+
+
+def test_argument_checks_need_no_gpu():
+    """Invalid arguments are rejected before any CUDA call."""
+    import ctypes as C
+    from paper_2506_11510_gb300 import _native as N
+    L = N.lib()
+    out = C.c_void_p()
+    desc = N.TgVolumeDesc()
+    desc.nx = desc.ny = desc.nz = 8
+    desc.voxel_size = 0.125
+    assert L.leb_build(None, C.byref(desc), None, 0.0, -1.0, 4, 0, None, C.byref(out)) == N.TG_EINVAL
+    assert L.leb_build(C.c_void_p(16), C.byref(desc), None, 0.0, -1.0, 51, 0, None, C.byref(out)) == N.TG_EINVAL
+    assert L.leb_build(C.c_void_p(16), C.byref(desc), None, 0.0, -1.0, 4, 3, None, C.byref(out)) == N.TG_EINVAL
+    assert L.tet_render(None, None, None, 1, 0, 0, None, None, None, None) == N.TG_EINVAL
+    assert L.tg_grid_info(None, None, None, None, None, None) == N.TG_EINVAL

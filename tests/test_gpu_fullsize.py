@@ -1,0 +1,181 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+adaptive (256^3 cloud, 512^2 at 32 spp, ~4.2 M tets): the whole GPU grid is
+compared bit for bit with the oracle's; a seeded subset of paths is compared
+one by one; and the full-frame render's accumulations at sampled pixels are
+compared with the oracle's sums over the same paths.
+
+production (1024x1024x512 cloud, 1024^2 at 32 spp, ~50 M tets, BF16): the
+oracle cannot build this grid in test time, so the GPU grid is checked by
+properties that hold at any size (exact volumes tiling the domain, symmetric
+links joining identical faces, orientation ids, planes, longest-edge
+refinement), and at sampled points against the oracle's own descent of the
+LEB hierarchy (the leaf holding a point is a node of the oracle's descent, the
+criterion does not split it, and its statistics and stored density are the
+oracle's).  The full-frame render is checked by its counters, the white
+furnace on sampled paths, and Beer-Lambert optical depths along sampled rays
+against brute-force clipping with every cell of the grid.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2506_11510_gb300 import workloads as W
+from tests import _checks_torch as CT
+from tests.test_gpu_render import FRAC, REL, compare_paths
+
+pytestmark = pytest.mark.gpu
+
+NTHREADS = os.cpu_count() or 8
+
+
+@pytest.fixture(scope="module")
+def adaptive():
+    import paper_2506_11510_gb300 as tv
+    s = W.scene("adaptive")
+    vol = W.make_volume(s, device="cuda")
+    grid = tv.build_scene_grid(s, vol)
+    vnp = vol.cpu().numpy()
+    ref = O.Grid.for_scene(s, vnp, nthreads=NTHREADS)
+    return s, vol, vnp, grid, ref
+
+
+def test_adaptive_volume_generation_is_device_independent(adaptive):
+    s, vol, vnp, _, _ = adaptive
+    cpu = W.make_volume(s, z_range=(100, 104)).numpy()
+    assert np.array_equal(cpu, vnp[100:104])
+
+
+def test_adaptive_grid_bit_exact(adaptive):
+    from tests.test_gpu_build import assert_same_grid, gpu_arrays
+    s, _, _, grid, ref = adaptive
+    a = ref.export()
+    assert 2_000_000 <= len(a.codes) <= 5_000_000
+    assert_same_grid(gpu_arrays(grid), a)
+
+
+def test_adaptive_sampled_paths_match_oracle(adaptive):
+    import paper_2506_11510_gb300 as tv
+    s, _, _, grid, ref = adaptive
+    px, py, sm = W.random_path_ids(s, 4096, seed=21)
+    got = tv.tet_trace_paths(grid, s.camera, s.medium, s.render_seed, px, py, sm, seq_cap=512)
+    want = ref.render_paths(s.camera, s.medium, s.render_seed, px.numpy(), py.numpy(), sm.numpy(), seq_cap=512,
+                            nthreads=NTHREADS)
+    compare_paths(got, want)
+
+
+def test_adaptive_full_frame_sampled_pixels(adaptive):
+    """The full 512^2 x 32 spp frame as bench.py renders it; at 64 random pixels the
+    accumulated sums equal the oracle's sums over the same 32 paths."""
+    import paper_2506_11510_gb300 as tv
+    s, _, _, grid, ref = adaptive
+    stats = tv.new_stats()
+    img, img2 = tv.tet_render(grid, s.camera, s.medium, s.spp, s.render_seed, stats=stats)
+    st = tv.stats_dict(stats)
+    assert st["paths"] == s.paths_per_frame and st["step_limit"] == 0
+    rng = np.random.default_rng(8)
+    pix = rng.integers(0, s.camera.width * s.camera.height, 64)
+    px = np.repeat(pix % s.camera.width, s.spp).astype(np.int32)
+    py = np.repeat(pix // s.camera.width, s.spp).astype(np.int32)
+    sm = np.tile(np.arange(s.spp), len(pix)).astype(np.int32)
+    want = ref.render_paths(s.camera, s.medium, s.render_seed, px, py, sm, nthreads=NTHREADS)
+    osum = want["L"].reshape(len(pix), s.spp).sum(1)
+    osq = (want["L"] ** 2).reshape(len(pix), s.spp).sum(1)
+    g = img.cpu().numpy().reshape(-1)[pix].astype(np.float64)
+    g2 = img2.cpu().numpy().reshape(-1)[pix].astype(np.float64)
+    close = np.abs(g - osum) <= 1e-3 * np.maximum(np.abs(osum), 1e-4)
+    assert close.mean() >= 0.95
+    assert np.allclose(g2, osq, rtol=1e-2, atol=1e-4) or np.mean(np.abs(g2 - osq) <= 1e-2 * np.abs(osq)) >= 0.95
+
+
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def production():
+    import paper_2506_11510_gb300 as tv
+    s = W.scene("production")
+    vol = W.make_volume(s, device="cuda")
+    grid = tv.build_scene_grid(s, vol)
+    return s, vol, grid
+
+
+def test_production_grid_properties(production):
+    s, _, grid = production
+    ex = grid.export(("codes", "verts", "tag", "nbr", "nid", "plane"))
+    n = ex["codes"].shape[0]
+    assert 20_000_000 <= n <= 80_000_000, n
+    CT.check_grid_torch(ex, grid.info.K, (2, 2, 1))
+    assert len(torch.unique(ex["nid"])) == 18
+
+
+def test_production_sampled_leaves_follow_the_oracle(production):
+    s, vol, grid = production
+    vnp = vol.cpu().numpy()
+    ex = grid.export(("codes", "density", "count", "sum", "qmin", "qmax"))
+    codes = ex["codes"].cpu().numpy().view(np.uint64)
+    rng = np.random.default_rng(31)
+    pts = rng.uniform([0, 0, 0], [2, 2, 1], (24, 3))
+    pr = O.path_profile(vnp, s.box_min, s.voxel_size, s.camera, s.footprint_px, s.variation_threshold, s.max_depth,
+                        s.density_format, pts, nthreads=NTHREADS)
+    pos = {int(c): i for i, c in enumerate(codes)}
+    for p in range(len(pts)):
+        hits = [d for d in range(s.max_depth + 1) if int(pr["codes"][p, d]) in pos]
+        assert len(hits) == 1, "the point's leaf is not a node of the oracle's descent"
+        d = hits[0]
+        i = pos[int(pr["codes"][p, d])]
+        assert pr["split"][p, d] == 0, "the criterion would split this leaf"
+        assert int(ex["count"][i]) == int(pr["count"][p, d]) and int(ex["sum"][i]) == int(pr["sum"][p, d])
+        assert int(ex["qmin"][i]) == int(pr["qmin"][p, d]) and int(ex["qmax"][i]) == int(pr["qmax"][p, d])
+        assert float(ex["density"][i]) == float(pr["density"][p, d])
+
+
+def test_production_full_frame_and_furnace(production):
+    import paper_2506_11510_gb300 as tv
+    s, _, grid = production
+    stats = tv.new_stats()
+    img, _ = tv.tet_render(grid, s.camera, s.medium, s.spp, s.render_seed, stats=stats)
+    st = tv.stats_dict(stats)
+    assert st["paths"] == s.paths_per_frame and st["step_limit"] == 0
+    assert bool(torch.isfinite(img).all()) and float(img.min()) >= 0
+    med = W.Medium(1.0, s.medium.g, s.medium.sigma_scale, 100000, s.medium.sun_dir, 0.0, 1.0)
+    px, py, sm = W.random_path_ids(s, 20000, seed=4)
+    out = tv.tet_trace_paths(grid, s.camera, med, 3, px, py, sm)
+    ok = (out["flags"].cpu().numpy() & 2) == 0
+    assert ok.mean() > 0.99 and np.all(out["L"].cpu().numpy()[ok] == 1.0)
+
+
+def test_production_optical_depth_by_brute_force(production):
+    import paper_2506_11510_gb300 as tv
+    s, _, grid = production
+    ex = grid.export(("verts", "density"))
+    K = grid.info.K
+    v = ex["verts"].to(torch.float64) * 2.0 ** (-K)
+    rho = ex["density"].to(torch.float64)
+    FACE = CT.FACE
+    rng = np.random.default_rng(12)
+    target = rng.uniform([0.1, 0.1, 0.1], [1.9, 1.9, 0.9], (16, 3))
+    d = rng.normal(size=(16, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = target - 3.0 * d
+    got = tv.tet_optical_depth(grid, torch.tensor(o, dtype=torch.float32, device="cuda"),
+                               torch.tensor(d, dtype=torch.float32, device="cuda"), 1.0)["tau"].cpu().numpy()
+    for r in range(len(o)):
+        oo = torch.tensor(o[r].astype(np.float32).astype(np.float64), device="cuda")
+        dd = torch.tensor(d[r].astype(np.float32).astype(np.float64), device="cuda")
+        dd = dd / dd.norm()
+        t0 = torch.full((v.shape[0],), -math.inf, dtype=torch.float64, device="cuda")
+        t1 = torch.full_like(t0, math.inf)
+        for f in range(4):
+            fv = v[:, FACE[f], :]
+            n = torch.cross(fv[:, 1] - fv[:, 0], fv[:, 2] - fv[:, 0], dim=1)
+            out = (n * (v[:, f] - fv[:, 0])).sum(1) > 0
+            n = torch.where(out[:, None], -n, n)
+            c = (n * fv[:, 0]).sum(1)
+            nd = n @ dd
+            t = (c - n @ oo) / nd
+            t1 = torch.where(nd > 0, torch.minimum(t1, t), t1)
+            t0 = torch.where(nd < 0, torch.maximum(t0, t), t0)
+        tau = float((rho * torch.clamp(t1 - t0, min=0)).sum())
+        assert got[r] == pytest.approx(tau, rel=1e-4, abs=1e-5)

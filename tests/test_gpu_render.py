@@ -1,0 +1,129 @@
+"""GPU path tracer (Sec. 3, Algorithm 1 + sun NEE) against the CPU oracle on the
+same grid and the same Philox streams: per-path estimates within 1e-4
+relative for >= 99.9% of paths, visited-cell sequences equal for
+non-degenerate paths, and image means inside a 3-sigma bound."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2506_11510_gb300 import workloads as W
+from tests.conftest import scene_volume
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4          # per-path tolerance (fp32 GPU walk against the fp64 oracle)
+FRAC = 0.999        # fraction of paths that must meet it
+
+
+def all_paths(cam, spp):
+    py, px, sm = np.meshgrid(np.arange(cam.height), np.arange(cam.width), np.arange(spp), indexing="ij")
+    return px.ravel().astype(np.int32), py.ravel().astype(np.int32), sm.ravel().astype(np.int32)
+
+
+def compare_paths(got, want, seq=True):
+    L = got["L"].cpu().numpy().astype(np.float64)
+    Lo = want["L"]
+    close = np.abs(L - Lo) <= REL * np.maximum(np.abs(Lo), 1e-6)
+    assert close.mean() >= FRAC, "only %.5f of paths within %g (worst %g)" % (
+        close.mean(), REL, np.max(np.abs(L - Lo)))
+    gf = got["flags"].cpu().numpy()
+    assert np.mean((gf & 0x1E) == (want["flags"] & 0x1E)) >= FRAC
+    assert np.mean(got["collisions"].cpu().numpy() == want["collisions"]) >= FRAC
+    # image mean of the per-path differences inside 3 sd / sqrt(n)
+    d = L - Lo
+    if d.std() > 0:
+        assert abs(d.mean()) <= 3 * d.std() / math.sqrt(len(d)) + 1e-7
+    if seq and "seq" in got:
+        nondeg = (want["flags"] & 1) == 0
+        gs, gl = got["seq"].cpu().numpy(), got["seq_len"].cpu().numpy()
+        same = np.array([np.array_equal(gs[i, :gl[i]], want["seq"][i, :want["seq_len"][i]]) for i in
+                         np.nonzero(nondeg)[0]])
+        assert nondeg.mean() > 0.5
+        assert same.mean() >= FRAC, "visited sequences differ on %.4f of non-degenerate paths" % (1 - same.mean())
+    return close.mean()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    import paper_2506_11510_gb300 as tv
+    s = W.scene("tiny")
+    vol = scene_volume("tiny")
+    grid = tv.build_scene_grid(s, torch.from_numpy(vol).cuda())
+    ref = O.Grid.for_scene(s, vol)
+    return s, grid, ref
+
+
+def test_tiny_all_paths_match_oracle(tiny):
+    import paper_2506_11510_gb300 as tv
+    s, grid, ref = tiny
+    px, py, sm = all_paths(s.camera, s.spp)
+    got = tv.tet_trace_paths(grid, s.camera, s.medium, s.render_seed, px, py, sm, seq_cap=512)
+    want = ref.render_paths(s.camera, s.medium, s.render_seed, px, py, sm, seq_cap=512)
+    compare_paths(got, want)
+
+
+def test_tiny_image_is_the_sum_of_its_paths(tiny):
+    """tet_render (persistent, regenerating warps, atomics) equals the per-path
+    estimates summed per pixel, and the oracle's image."""
+    import paper_2506_11510_gb300 as tv
+    s, grid, ref = tiny
+    stats = tv.new_stats()
+    img, img2 = tv.tet_render(grid, s.camera, s.medium, s.spp, s.render_seed, stats=stats)
+    oimg, oimg2, osteps = ref.render(s.camera, s.medium, s.spp, s.render_seed)
+    st = tv.stats_dict(stats)
+    assert st["paths"] == s.camera.width * s.camera.height * s.spp
+    assert st["step_limit"] == 0
+    g = img.cpu().numpy().astype(np.float64)
+    close = np.abs(g - oimg) <= 1e-4 * np.maximum(np.abs(oimg), 1e-5) + 1e-6
+    assert close.mean() >= 0.999
+    # progressive accumulation: two calls of spp/2 samples each give the same image
+    a, a2 = tv.tet_render(grid, s.camera, s.medium, 2, s.render_seed, sample_offset=0)
+    tv.tet_render(grid, s.camera, s.medium, 2, s.render_seed, sample_offset=2, accum_sum=a, accum_sumsq=a2)
+    assert torch.allclose(a, img, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("name", ["adaptive_small", "production_small"])
+def test_small_scenes_all_paths_match_oracle(name):
+    import paper_2506_11510_gb300 as tv
+    s = W.scene(name)
+    vol = scene_volume(name)
+    grid = tv.build_scene_grid(s, torch.from_numpy(vol).cuda())
+    ref = O.Grid.for_scene(s, vol)
+    px, py, sm = all_paths(s.camera, s.spp)
+    got = tv.tet_trace_paths(grid, s.camera, s.medium, s.render_seed, px, py, sm, seq_cap=256)
+    want = ref.render_paths(s.camera, s.medium, s.render_seed, px, py, sm, seq_cap=256)
+    compare_paths(got, want)
+
+
+def test_white_furnace_on_gpu(tiny):
+    import paper_2506_11510_gb300 as tv
+    s, grid, _ = tiny
+    med = W.Medium(1.0, 0.3, 30.0, 100000, s.medium.sun_dir, 0.0, 1.0)
+    px, py, sm = all_paths(s.camera, 2)
+    got = tv.tet_trace_paths(grid, s.camera, med, 11, px, py, sm)
+    L = got["L"].cpu().numpy()
+    ok = (got["flags"].cpu().numpy() & 2) == 0
+    assert ok.mean() > 0.999
+    assert np.all(L[ok] == 1.0)
+
+
+def test_empty_grid_and_misses():
+    import paper_2506_11510_gb300 as tv
+    vol = torch.zeros((16, 16, 16), device="cuda")
+    s = W.scene("adaptive_small", dims=(16, 16, 16), voxel_size=1 / 16)
+    grid = tv.leb_build(vol, (0, 0, 0), 1 / 16, s.camera, 1.0, 0.5, 12, 0)
+    assert grid.info.num_tets == 6
+    img, _ = tv.tet_render(grid, s.camera, s.medium, 2, 3)
+    assert torch.allclose(img, torch.full_like(img, 2 * s.medium.env_radiance))
+
+
+def test_zero_work_calls_are_noops(tiny):
+    import paper_2506_11510_gb300 as tv
+    s, grid, _ = tiny
+    img, _ = tv.tet_render(grid, s.camera, s.medium, 0, 1)
+    assert float(img.abs().sum()) == 0.0
+    out = tv.tet_trace_paths(grid, s.camera, s.medium, 1, [], [], [])
+    assert out["L"].numel() == 0
