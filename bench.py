@@ -288,12 +288,11 @@ def grid_max_depth(ntets, s):
 # ---------------------------------------------------------------------------
 # the oracle (CPU) on a bounded sample of the workload
 # ---------------------------------------------------------------------------
-def oracle_sample(s, vol_np, side, nthreads=0):
-    """Oracle grid for a side x side pixel window at the centre of the frame (the
-    camera criterion refines the window's sub-frustum only) and the window's
-    paths at the frame's spp.  Returns (paths, render seconds, build seconds)."""
-    import numpy as np
-
+def oracle_window(s, vol_np, side, nthreads=0):
+    """The oracle's grid for a side x side pixel window at the centre of the frame:
+    the camera criterion refines the window's sub-frustum only, so outside it the
+    grid stays coarse (cheaper paths than the full frame's).  Returns the grid,
+    the window camera and the build time."""
     import oracle as O
     from paper_2506_11510_gb300 import workloads as W
     cam = s.camera
@@ -302,28 +301,33 @@ def oracle_sample(s, vol_np, side, nthreads=0):
     wcam = W.Camera(cam.pos, cam.target, cam.up, fov, side, side)
     t0 = time.time()
     g = O.Grid.for_scene(s, vol_np, camera=wcam, nthreads=nthreads)
-    tb = time.time() - t0
+    return g, wcam, time.time() - t0
+
+
+def oracle_window_render(s, g, wcam, nthreads=0):
+    """All paths of the window at the frame's spp; returns (paths, seconds)."""
+    import numpy as np
+    side = wcam.width
     py, px, sm = np.meshgrid(np.arange(side), np.arange(side), np.arange(s.spp), indexing="ij")
     t0 = time.time()
     g.render_paths(wcam, s.medium, s.render_seed, px.ravel(), py.ravel(), sm.ravel(), nthreads=nthreads)
-    tr = time.time() - t0
-    return side * side * s.spp, tr, tb
+    return side * side * s.spp, time.time() - t0
+
+
+def cpu_sample_text(side, s, paths, tb):
+    return ("%dx%d-pixel window at the frame centre, %d spp (%d paths), on the oracle's grid refined for the "
+            "window's sub-frustum only (coarse elsewhere, so paths are cheaper than the full frame's; built once "
+            "in %.0f s, not timed); fp64 C++, OpenMP over paths" % (side, side, s.spp, paths, tb))
 
 
 def cpu_baseline(args, s, vol):
     vol_np = vol.cpu().numpy() if hasattr(vol, "cpu") else vol
     cores = os.cpu_count() or 1
-    side = args.cpu_sample_px or 16
-    paths, tr, tb = oracle_sample(s, vol_np, side)
-    # grow the window until the render takes ~10 s of wall time (bounded)
-    while tr < 3.0 and side < 128 and not args.cpu_sample_px:
-        side *= 2
-        paths, tr, tb = oracle_sample(s, vol_np, side)
+    side = args.cpu_sample_px or 64
+    g, wcam, tb = oracle_window(s, vol_np, side)
+    paths, tr = oracle_window_render(s, g, wcam)
     return {"value": round(paths / tr / 1e6, 5), "unit": "Mpaths/s", "cores": cores, "kind": "oracle",
-            "sample": "%dx%d-pixel window at the frame centre, %d spp (%d paths), on the oracle's grid for the "
-                      "window's sub-frustum (built in %.1f s, not timed); fp64 C++, OpenMP over paths"
-                      % (side, side, s.spp, paths, tb),
-            "render_s": round(tr, 2)}
+            "sample": cpu_sample_text(side, s, paths, tb), "render_s": round(tr, 2)}
 
 
 def run_reference(args):
@@ -338,12 +342,13 @@ def run_reference(args):
     except Exception:
         dev = "cpu"
     vol = W.make_volume(s, device=dev).cpu().numpy()
-    side = args.cpu_sample_px or 16
+    side = args.cpu_sample_px or 64
+    g, wcam, tb = oracle_window(s, vol, side)
     for _ in range(args.warmup):
-        pass
+        oracle_window_render(s, g, wcam)
     times, paths = [], 0
     for _ in range(max(1, args.steps)):
-        paths, tr, tb = oracle_sample(s, vol, side)
+        paths, tr = oracle_window_render(s, g, wcam)
         times.append(tr)
     mean = sum(times) / len(times)
     value = paths / mean / 1e6
@@ -352,9 +357,9 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": round(mean * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_name(s, 0) + " -- oracle on a %dx%d-pixel window" % (side, side)},
+            "config": {"workload": workload_name(s, 0) + " -- the CPU oracle on a %dx%d-pixel window" % (side, side)},
             "cpu_baseline": {"value": round(value, 5), "unit": "Mpaths/s", "cores": cores, "kind": "oracle",
-                             "sample": "%dx%d-pixel window, %d spp per step" % (side, side, s.spp)},
+                             "sample": cpu_sample_text(side, s, paths, tb)},
             "e2e": {"value": round(value, 5), "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -2,6 +2,7 @@
 // Philox4x32-10, Henyey-Greenstein sampling, camera set-up.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
