@@ -195,6 +195,28 @@ int tet_optical_depth(const tg_grid* g, int64_t n, const float* origin, const fl
                       float* tau, int64_t* steps, int32_t* seq, int32_t seq_cap, int32_t* seq_len,
                       void* cuda_stream);
 
+/*
+ * tet_render_noalloc - the frame of tet_render, for callers that may not let a
+ * library allocate device memory (applications that hand out all device memory
+ * from their own pool or budget, and loops that cannot afford the implicit
+ * synchronisation of cudaMalloc).  The paper has no counterpart: this is a
+ * property of the library, not of the method.
+ *   Allocates nothing.  Its scratch (the estimator's path counter and 16 bytes
+ *   per path) is a static device array of TG_NOALLOC_MAX_PATHS paths (8 MiB),
+ *   held by every device that loads the library until the process exits.
+ *   W * H * spp above TG_NOALLOC_MAX_PATHS is rejected with TG_EINVAL.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   All calls share the array and its contents persist between calls: calls
+ *   that overlap on the GPU (other streams, other threads) race.  Serialise them.
+ *   Same arguments and accumulation (+=) as tet_render, without stats; each
+ *   pixel's samples are summed in sample order, so the image is the same from
+ *   run to run.
+ */
+#define TG_NOALLOC_MAX_PATHS (1 << 19)
+int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp, uint64_t seed,
+                       int32_t sample_offset, float* accum_sum, float* accum_sumsq, void* cuda_stream);
+
 const char* tg_error_string(int status);
 
 #ifdef __cplusplus
