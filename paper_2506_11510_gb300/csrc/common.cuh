@@ -192,6 +192,12 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return fast_two_sum(r.hi, __fadd_rn(r.lo, t.lo));
 }
 
+// cheaper sum for operands of equal sign (accumulating optical depths)
+__device__ __forceinline__ ff ff_add_fast(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 

@@ -42,6 +42,7 @@ static EstParams dda_est(const tg_camera& cam, const tg_medium& med, uint64_t se
   ep.med = medium_setup(med, cube);
   ep.seed = seed;
   ep.regen_min = 8;
+  ep.ev_min = 8;
   return ep;
 }
 

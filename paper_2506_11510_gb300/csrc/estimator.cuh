@@ -20,13 +20,22 @@
 // fp32: their errors are not amplified.  GB300's FP64 rate is far too low for
 // the per-cell loop; shadow walks are the majority of all cell steps.
 //
+// SIMD efficiency.  A warp keeps 32 paths in flight, each in one of four
+// states: idle (waiting for a path id), walking, event (waiting for the warp
+// to process a collision, an escape or the end of a shadow walk) and done.
+// Free flights and shadow walks share one step: a segment walks cells from
+// parameter 0, accumulating optical depth until a limit (the sampled free path,
+// or the shadow cut-off) or the boundary, with all four faces evaluated under
+// predication.  Events and new paths are batched: a warp handles them when at
+// least regen_min / ev_min lanes wait (or nothing else can run), so the long,
+// branchy event code runs with many lanes at once.
+//
 // Walker interface (tetrahedra: walk_tet.cuh, voxels: walk_voxel.cuh):
 //   bool intersect(o, d, &t_in)   slab test with the domain box (fp32)
 //   bool locate(p)                current cell := the cell that holds p
-//   void begin_free(o, d)         per-segment tables for the free flight o + t d
-//   Hop  hop_free(t)              exit parameter of the current cell
-//   void begin_shadow(o, w)       fp32 tables for the shadow ray towards w
-//   Hop  hop_shadow(t)            fp32 exit parameter of the current cell
+//   void dir_table(d, inv, &m)    direction table of a segment (NDIR floats + mask)
+//   void begin(o, inv, m)         per-thread segment table for the ray o + t d
+//   Hop  hop(t)                   exit parameter of the current cell from t
 //   bool advance()                move to the pending cell (false: boundary)
 //   int  save() / restore(c)      remember / return to a cell
 //   int  cell()                   current cell id (for traces)
@@ -41,7 +50,9 @@ constexpr int SEG_STEP_LIMIT = 1 << 20;      // cells per segment before a walk 
 // E * beta * p * e^-40 < 1e-16 and is stopped early (not in trace mode).
 constexpr float SHADOW_TAU_CUTOFF = 40.0f;
 
-enum : int { S_IDLE = 0, S_FREE = 1, S_SHADOW = 2, S_DONE = 3 };
+enum : int { S_IDLE = 0, S_WALK = 1, S_EVENT = 2, S_DONE = 3 };
+enum : int { M_FREE = 0, M_SHADOW = 1 };
+enum : int { EV_LIMIT = 1, EV_BOUNDARY = 2 };
 
 struct Hop {
   float texit;
@@ -60,6 +71,7 @@ struct EstParams {
   float* sumsq;
   tg_stats* stats;
   int regen_min;                            // idle lanes needed before a warp refills
+  int ev_min;                               // waiting lanes needed before a warp handles events
   // trace mode (per-path outputs for a list of paths)
   const int32_t *px, *py, *ps;
   float* outL;
@@ -98,26 +110,36 @@ __device__ __forceinline__ bool box_intersect(const int C[3], float3 o, float3 d
 template <class Walker, bool TRACE>
 __global__ void __launch_bounds__(EST_BLOCK) k_estimate(const typename Walker::Params wp, const EstParams ep) {
   extern __shared__ double smem_d[];
+  __shared__ float sun_inv[Walker::NDIR];
+  __shared__ uint32_t sun_mask;
   Walker W(wp, smem_d);
+  const MedF& M = ep.med;
+  if (threadIdx.x == 0) {
+    const ff3 w = {ff_make(M.sun_w[0]), ff_make(M.sun_w[1]), ff_make(M.sun_w[2])};
+    float inv[Walker::NDIR];
+    uint32_t m;
+    W.dir_table(w, inv, &m);
+    for (int i = 0; i < Walker::NDIR; ++i) sun_inv[i] = inv[i];
+    sun_mask = m;
+  }
+  __syncthreads();
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
-  const MedF& M = ep.med;
+  const ff sig_unit = ff{M.sig_hi, M.sig_lo};
 
-  int state = S_IDLE;
+  int state = S_IDLE, mode = M_FREE, ev = 0;
   long long pid = 0;
   uint32_t pixel = 0, sample = 0;
   ff3 o = {ff_make(0.f), ff_make(0.f), ff_make(0.f)};   // segment origin
   ff3 d = o;                                           // path direction (float-float on camera rays)
-  float t = 0.f;                                       // free flight: parameter
-  ff tau = ff_make(0.f);                               // free flight: optical depth left
-  float ts = 0.f, od = 0.f;                            // shadow walk: parameter, optical depth so far
+  float t = 0.f;                                       // segment parameter
+  ff acc = ff_make(0.f);                               // optical depth of the segment so far
+  float lim = 0.f;                                     // its limit: free path, or shadow cut-off
   float beta = 1.f;
   ff L = ff_make(0.f);
-  const ff sig_unit = ff{M.sig_hi, M.sig_lo};
   int bounce = 0, seg_steps = 0, flags = 0, ncoll = 0, saved = 0, seqn = 0;
   long long psteps = 0;
-  unsigned long long c_paths = 0, c_steps = 0, c_shadow = 0, c_coll = 0, c_esc = 0, c_trunc = 0, c_lim = 0,
-                     c_miss = 0;
+  uint32_t c_paths = 0, c_steps = 0, c_shadow = 0, c_coll = 0, c_esc = 0, c_trunc = 0, c_lim = 0, c_miss = 0;
 
   auto record = [&](int v) {
     if (TRACE) {
@@ -140,18 +162,24 @@ __global__ void __launch_bounds__(EST_BLOCK) k_estimate(const typename Walker::P
     }
     state = S_IDLE;
   };
-  auto new_flight = [&](int b) {
+  // a free flight from o along d: SampleFreePath gives the optical depth to consume
+  auto start_free = [&](int b) {
+    float inv[Walker::NDIR];
+    uint32_t m;
+    W.dir_table(d, inv, &m);
+    W.begin(o, inv, m);
     t = 0.f;
-    tau = ff_make(-logf(1.0f - rng_u(ep.seed, pixel, sample, 2 + 3 * b)));   // SampleFreePath
+    acc = ff_make(0.f);
+    lim = -logf(1.0f - rng_u(ep.seed, pixel, sample, 2 + 3 * b));
     seg_steps = 0;
-    W.begin_free(o, d);
-    state = S_FREE;
+    mode = M_FREE;
+    state = S_WALK;
   };
 
   for (;;) {
     // ---- regeneration: idle lanes of the warp take consecutive path ids ----
     const unsigned idle = __ballot_sync(~0u, state == S_IDLE);
-    const unsigned busy = __ballot_sync(~0u, state == S_FREE || state == S_SHADOW);
+    const unsigned busy = __ballot_sync(~0u, state == S_WALK || state == S_EVENT);
     if (idle && (busy == 0 || __popc(idle) >= ep.regen_min)) {
       const int leader = __ffs(idle) - 1;
       unsigned long long base = 0;
@@ -201,74 +229,83 @@ __global__ void __launch_bounds__(EST_BLOCK) k_estimate(const typename Walker::P
               flags = 16;
               finish();
             } else {
-              new_flight(0);
+              start_free(0);
             }
           }
         }
       }
     }
-    if (__all_sync(~0u, state == S_DONE)) break;
-    if (state != S_FREE && state != S_SHADOW) continue;
 
-    record(W.cell());
-    ++seg_steps; ++psteps;
-    if (state == S_FREE) {
-      // ---- one cell of MarchThroughCells: ReadDensity, consume the free path ----
-      ++c_steps;
-      const Hop h = W.hop_free(t);
-      if (!h.ok) { flags |= 16; finish(); continue; }
-      const ff sig = ff_mul_f(sig_unit, h.rho);
-      const ff dtau = ff_mul_f(sig, h.texit - t);
-      if (h.rho > 0.f && !ff_lt(dtau, tau)) {
-        // collision: albedo weight, then next-event estimation towards the sun
-        const ff tc = ff_add(ff_make(t), ff_div(tau, sig));
-        o = ff3{ff_add(o.x, ff_mul(tc, d.x)), ff_add(o.y, ff_mul(tc, d.y)), ff_add(o.z, ff_mul(tc, d.z))};
-        beta *= M.albedo;
-        ++ncoll; ++c_coll;
+    // ---- events, handled together by the lanes that wait for one ----
+    const unsigned pend = __ballot_sync(~0u, state == S_EVENT);
+    const unsigned walking = __ballot_sync(~0u, state == S_WALK);
+    if (pend && (walking == 0 || __popc(pend) >= ep.ev_min) && state == S_EVENT) {
+      if (mode == M_FREE) {
+        if (ev == EV_LIMIT) {
+          // collision at parameter acc: albedo weight, then next-event estimation towards the sun
+          o = ff3{ff_add(o.x, ff_mul(acc, d.x)), ff_add(o.y, ff_mul(acc, d.y)), ff_add(o.z, ff_mul(acc, d.z))};
+          beta *= M.albedo;
+          ++ncoll; ++c_coll;
+          record(-1);
+          saved = W.save();
+          W.begin(o, sun_inv, sun_mask);
+          t = 0.f;
+          acc = ff_make(0.f);
+          lim = TRACE ? INFINITY : SHADOW_TAU_CUTOFF;
+          seg_steps = 0;
+          mode = M_SHADOW;
+          state = S_WALK;
+        } else {
+          L = ff_add(L, ff_make(beta * M.Lenv)); ++c_esc;
+          finish();
+        }
+      } else {
+        // the shadow walk ended: add the sun seen through it
         record(-1);
-        saved = W.save();
-        W.begin_shadow(o, make_float3(M.sun_w[0], M.sun_w[1], M.sun_w[2]));
-        ts = 0.f; od = 0.f; seg_steps = 0;
-        state = S_SHADOW;
-        continue;
-      }
-      tau = ff_sub(tau, dtau);
-      t = h.texit;
-      if (!W.advance()) {
-        L = ff_add(L, ff_make(beta * M.Lenv)); ++c_esc;
-        finish();
-        continue;
-      }
-    } else {
-      // ---- one cell of the shadow walk (transmittance to the boundary) ----
-      ++c_shadow;
-      const Hop h = W.hop_shadow(ts);
-      if (!h.ok) { flags |= 16; finish(); continue; }
-      od += M.sig_hi * h.rho * (h.texit - ts);
-      ts = h.texit;
-      const bool out = !W.advance();
-      if (out || (!TRACE && od > SHADOW_TAU_CUTOFF)) {
-        record(-1);
-        const float tr = out ? expf(-od) : 0.0f;
+        const float tr = ev == EV_BOUNDARY ? expf(-ff_float(acc)) : 0.0f;
         const float cs = d.x.hi * M.sun_w[0] + d.y.hi * M.sun_w[1] + d.z.hi * M.sun_w[2];
         L = ff_add(L, ff_make(beta * hg_eval(M.g, cs) * M.E * tr));
         if (bounce + 1 >= M.max_bounces) {
           flags |= 2; ++c_trunc;
           finish();
-          continue;
+        } else {
+          // SamplePhaseFunction, then a new free flight from the collision point
+          const float3 nd = hg_scatter(M.g, rng_u(ep.seed, pixel, sample, 3 + 3 * bounce),
+                                       rng_u(ep.seed, pixel, sample, 4 + 3 * bounce),
+                                       make_float3(d.x.hi, d.y.hi, d.z.hi));
+          d = ff3{ff_make(nd.x), ff_make(nd.y), ff_make(nd.z)};
+          ++bounce;
+          W.restore(saved);
+          start_free(bounce);
         }
-        // SamplePhaseFunction, then a new free flight from the collision point
-        const float3 nd = hg_scatter(M.g, rng_u(ep.seed, pixel, sample, 3 + 3 * bounce),
-                                     rng_u(ep.seed, pixel, sample, 4 + 3 * bounce),
-                                     make_float3(d.x.hi, d.y.hi, d.z.hi));
-        d = ff3{ff_make(nd.x), ff_make(nd.y), ff_make(nd.z)};
-        ++bounce;
-        W.restore(saved);
-        new_flight(bounce);
-        continue;
       }
     }
-    if (seg_steps >= SEG_STEP_LIMIT) {
+    if (__all_sync(~0u, state == S_DONE)) break;
+    if (state != S_WALK) continue;
+
+    // ---- one cell: ReadDensity and MarchThroughCells (or the shadow walk) ----
+    record(W.cell());
+    ++seg_steps;
+    if (TRACE) ++psteps;
+    const Hop h = W.hop(t);
+    if (!h.ok) { flags |= 16; finish(); continue; }
+    if (mode == M_FREE) ++c_steps; else ++c_shadow;
+    const ff sig = ff_mul_f(sig_unit, h.rho);
+    const ff dtau = ff_mul_f(sig, h.texit - t);
+    const ff sum = ff_add_fast(acc, dtau);
+    if (h.rho > 0.f && !ff_lt(sum, ff_make(lim))) {
+      // the segment's optical-depth limit falls inside this cell
+      if (mode == M_FREE) acc = ff_add(ff_make(t), ff_div(ff_sub(ff_make(lim), acc), sig));
+      ev = EV_LIMIT;
+      state = S_EVENT;
+      continue;
+    }
+    acc = sum;
+    t = h.texit;
+    if (!W.advance()) {
+      ev = EV_BOUNDARY;
+      state = S_EVENT;
+    } else if (seg_steps >= SEG_STEP_LIMIT) {
       flags |= 8; ++c_lim;
       finish();
     }

@@ -96,6 +96,7 @@ extern "C" int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const 
     ep.med = medium_setup(*med, G.cube);
     ep.seed = seed;
     ep.regen_min = 8;
+    ep.ev_min = 8;
     ep.spp = 1;
     ep.total = n;
     ep.counter = counter;

@@ -102,6 +102,7 @@ static EstParams est_params(const GridImpl& g, const tg_camera& cam, const tg_me
   ep.med = medium_setup(med, g.cube);
   ep.seed = seed;
   ep.regen_min = 8;
+  ep.ev_min = 8;
   return ep;
 }
 
@@ -128,12 +129,15 @@ __global__ void __launch_bounds__(EST_BLOCK) k_optical_depth(const TetParams P, 
     const ff3 e = {ff_add(ff_make(o.x), two_prod(tin, d.x)), ff_add(ff_make(o.y), two_prod(tin, d.y)),
                    ff_add(ff_make(o.z), two_prod(tin, d.z))};
     if (W.locate(make_float3(ff_float(e.x), ff_float(e.y), ff_float(e.z)))) {
-      W.begin_shadow(e, d);
+      float tinv[TetWalker<FMT>::NDIR];
+      uint32_t m;
+      W.dir_table(ff3{ff_make(d.x), ff_make(d.y), ff_make(d.z)}, tinv, &m);
+      W.begin(e, tinv, m);
       float t = 0.f;
       for (; k < SEG_STEP_LIMIT; ++k) {
         if (seq && len < seq_cap) seq[i * seq_cap + len] = W.cell();
         ++len;
-        const Hop h = W.hop_shadow(t);
+        const Hop h = W.hop(t);
         if (!h.ok) break;
         od += sigma * h.rho * (h.texit - t);
         t = h.texit;

@@ -126,9 +126,27 @@ inline __device__ long long tet_locate(const TetParams& P, float3 p) {
   return lo - 1;
 }
 
+// Orientation table of a direction: invND[p] = 2^-K / (P[p] . d) (the reciprocal
+// is correctly rounded and 2^-K exact) and the mask of orientation ids p | s << 4
+// whose outward normal points along d.
+__device__ __forceinline__ void tet_dir_table(const ff3& d, float invK, float inv[9], uint32_t* mask) {
+  const float nd[9] = {ff_float(d.x), ff_float(d.y), ff_float(d.z), ff_float(ff_add(d.x, d.y)),
+                       ff_float(ff_sub(d.x, d.y)), ff_float(ff_add(d.y, d.z)), ff_float(ff_sub(d.y, d.z)),
+                       ff_float(ff_add(d.x, d.z)), ff_float(ff_sub(d.x, d.z))};
+  uint32_t m = 0;
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    inv[p] = __frcp_rn(nd[p]) * invK;
+    m |= (nd[p] > 0.f ? 1u : 0u) << p;
+    m |= (nd[p] < 0.f ? 1u : 0u) << (p + 16);
+  }
+  *mask = m;
+}
+
 template <int FMT>
 struct TetWalker {
   using Params = TetParams;
+  static constexpr int NDIR = 9;            // direction-table entries
   const TetParams& P;
   double* tab;         // this thread's column: slot q at tab[q * EST_BLOCK], 18 slots
   uint32_t mask;
@@ -140,12 +158,8 @@ struct TetWalker {
 
   __device__ __forceinline__ float& ftab(int q) { return *reinterpret_cast<float*>(tab + q * EST_BLOCK); }
   __device__ __forceinline__ float ftab(int q) const { return *reinterpret_cast<const float*>(tab + q * EST_BLOCK); }
-
   __device__ __forceinline__ float2& pair(int q) { return *reinterpret_cast<float2*>(tab + q * EST_BLOCK); }
-  __device__ __forceinline__ ff pair_ff(int q) const {
-    const float2 v = *reinterpret_cast<const float2*>(tab + q * EST_BLOCK);
-    return ff{v.x, v.y};
-  }
+  __device__ __forceinline__ float2 pair(int q) const { return *reinterpret_cast<const float2*>(tab + q * EST_BLOCK); }
 
   __device__ bool intersect(float3 o, float3 d, float* t_in) const { return box_intersect(P.C, o, d, t_in); }
 
@@ -155,35 +169,19 @@ struct TetWalker {
     return c >= 0;
   }
 
-  // nO[p] = (P[p] . o) 2^K as a float-float pair, invND[p] = 2^-K / (P[p] . d) as a float
-  __device__ void begin_free(const ff3& o, const ff3& d) {
+  __device__ __forceinline__ void dir_table(const ff3& d, float inv[9], uint32_t* m) const {
+    tet_dir_table(d, P.invK, inv, m);
+  }
+
+  // Per-segment table: nO[p] = (P[p] . o) 2^K as a float-float pair (so c - nO is
+  // accurate to the distance walked, not to |o|), and the direction table.
+  __device__ void begin(const ff3& o, const float inv[9], uint32_t m) {
     const ff no[9] = {o.x, o.y, o.z, ff_add(o.x, o.y), ff_sub(o.x, o.y), ff_add(o.y, o.z), ff_sub(o.y, o.z),
                       ff_add(o.x, o.z), ff_sub(o.x, o.z)};
-    const float nd[9] = {ff_float(d.x), ff_float(d.y), ff_float(d.z), ff_float(ff_add(d.x, d.y)),
-                         ff_float(ff_sub(d.x, d.y)), ff_float(ff_add(d.y, d.z)), ff_float(ff_sub(d.y, d.z)),
-                         ff_float(ff_add(d.x, d.z)), ff_float(ff_sub(d.x, d.z))};
-    uint32_t m = 0;
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
       pair(p) = make_float2(no[p].hi * P.scaleK, no[p].lo * P.scaleK);
-      ftab(9 + p) = __fdiv_rn(P.invK, nd[p]);
-      m |= (nd[p] > 0.f ? 1u : 0u) << p;
-      m |= (nd[p] < 0.f ? 1u : 0u) << (p + 16);
-    }
-    mask = m;
-  }
-
-  __device__ void begin_shadow(const ff3& o, float3 w) {
-    const ff no[9] = {o.x, o.y, o.z, ff_add(o.x, o.y), ff_sub(o.x, o.y), ff_add(o.y, o.z), ff_sub(o.y, o.z),
-                      ff_add(o.x, o.z), ff_sub(o.x, o.z)};
-    const float nd[9] = {w.x, w.y, w.z, w.x + w.y, w.x - w.y, w.y + w.z, w.y - w.z, w.x + w.z, w.x - w.z};
-    uint32_t m = 0;
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-      ftab(p) = ff_float(no[p]) * P.scaleK;
-      ftab(9 + p) = __fdiv_rn(P.invK, nd[p]);
-      m |= (nd[p] > 0.f ? 1u : 0u) << p;
-      m |= (nd[p] < 0.f ? 1u : 0u) << (p + 16);
+      ftab(9 + p) = inv[p];
     }
     mask = m;
   }
@@ -193,7 +191,10 @@ struct TetWalker {
     b = __ldg(P.rec + 2 * (size_t)cur + 1);
   }
 
-  __device__ __forceinline__ Hop hop_free(float t) {
+  // Exit of the current cell from parameter t.  All four faces are evaluated and
+  // the ones whose outward normal does not face the ray are masked out, so the
+  // lanes of a warp execute one instruction stream.
+  __device__ __forceinline__ Hop hop(float t) {
     uint4 a, b;
     load(a, b);
     const uint32_t link[4] = {a.x, a.y, a.z, a.w};
@@ -204,37 +205,13 @@ struct TetWalker {
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const uint32_t id = link[f] >> 27;
-      if ((mask >> id) & 1u) {
-        const int p = (int)(id & 15u);
-        const float2 no = *reinterpret_cast<const float2*>(tab + p * EST_BLOCK);
-        const float tf = __fsub_rn(__fsub_rn((float)c[f], no.x), no.y) * ftab(9 + p);
-        if (tf < best) { best = tf; blink = link[f]; }
-      }
-    }
-    nxt = (int)(blink & NO_NBR);
-    Hop h;
-    h.ok = best < INFINITY;
-    h.texit = fmaxf(best, t);
-    h.rho = decode_density<FMT>(b.w);
-    return h;
-  }
-
-  __device__ __forceinline__ Hop hop_shadow(float t) {
-    uint4 a, b;
-    load(a, b);
-    const uint32_t link[4] = {a.x, a.y, a.z, a.w};
-    const int c[4] = {sext24(b.x), sext24((b.x >> 24) | (b.y << 8)), sext24((b.y >> 16) | (b.z << 16)),
-                      sext24(b.z >> 8)};
-    float best = INFINITY;
-    uint32_t blink = NO_NBR;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const uint32_t id = link[f] >> 27;
-      if ((mask >> id) & 1u) {
-        const int p = (int)(id & 15u);
-        const float tf = ((float)c[f] - ftab(p)) * ftab(9 + p);
-        if (tf < best) { best = tf; blink = link[f]; }
-      }
+      const int p = (int)(id & 15u);
+      const float2 no = pair(p);
+      float tf = __fmul_rn(__fsub_rn(__fsub_rn((float)c[f], no.x), no.y), ftab(9 + p));
+      tf = ((mask >> id) & 1u) ? tf : INFINITY;
+      const bool better = tf < best;
+      best = better ? tf : best;
+      blink = better ? link[f] : blink;
     }
     nxt = (int)(blink & NO_NBR);
     Hop h;

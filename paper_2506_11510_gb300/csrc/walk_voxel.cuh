@@ -17,9 +17,9 @@ struct VoxParams {
 
 struct VoxelWalker {
   using Params = VoxParams;
+  static constexpr int NDIR = 4;            // direction-table entries: 1/d.x, 1/d.y, 1/d.z, sign bits
   const VoxParams& P;
-  double* tab;        // 8-byte slots: o.x, o.y, o.z, 1/d.x, 1/d.y, 1/d.z (float-float pairs, or
-                      // floats in shadow walks)
+  double* tab;        // 8-byte slots: o.x, o.y, o.z as float-float pairs, then 1/d.x, 1/d.y, 1/d.z
   int ix, iy, iz;
   int axis;           // pending step axis
   int dir;            // bit a: d_a > 0, bit 3 + a: d_a < 0
@@ -31,12 +31,8 @@ struct VoxelWalker {
 
   __device__ __forceinline__ float& ftab(int q) { return *reinterpret_cast<float*>(tab + q * EST_BLOCK); }
   __device__ __forceinline__ float ftab(int q) const { return *reinterpret_cast<const float*>(tab + q * EST_BLOCK); }
-
   __device__ __forceinline__ float2& pair(int q) { return *reinterpret_cast<float2*>(tab + q * EST_BLOCK); }
-  __device__ __forceinline__ ff pair_ff(int q) const {
-    const float2 v = *reinterpret_cast<const float2*>(tab + q * EST_BLOCK);
-    return ff{v.x, v.y};
-  }
+  __device__ __forceinline__ float2 pair(int q) const { return *reinterpret_cast<const float2*>(tab + q * EST_BLOCK); }
 
   __device__ bool intersect(float3 o, float3 d, float* t_in) const { return box_intersect(P.C, o, d, t_in); }
 
@@ -53,64 +49,49 @@ struct VoxelWalker {
     return true;
   }
 
-  __device__ void begin_free(const ff3& o, const ff3& dd) {
+  __device__ __forceinline__ void dir_table(const ff3& dd, float inv[4], uint32_t* m) const {
+    const float d[3] = {ff_float(dd.x), ff_float(dd.y), ff_float(dd.z)};
+    uint32_t bits = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      inv[a] = d[a] != 0.f ? __frcp_rn(d[a]) : INFINITY;
+      bits |= (d[a] > 0.f ? 1u : 0u) << a;
+      bits |= (d[a] < 0.f ? 1u : 0u) << (3 + a);
+    }
+    inv[3] = 0.f;
+    *m = bits;
+  }
+
+  __device__ void begin(const ff3& o, const float inv[4], uint32_t bits) {
     pair(0) = make_float2(o.x.hi, o.x.lo);
     pair(1) = make_float2(o.y.hi, o.y.lo);
     pair(2) = make_float2(o.z.hi, o.z.lo);
-    const float3 d = make_float3(ff_float(dd.x), ff_float(dd.y), ff_float(dd.z));
-    ftab(3) = __fdiv_rn(1.0f, d.x);
-    ftab(4) = __fdiv_rn(1.0f, d.y);
-    ftab(5) = __fdiv_rn(1.0f, d.z);
-    dir = (d.x > 0.f) | ((d.y > 0.f) << 1) | ((d.z > 0.f) << 2) | ((d.x < 0.f) << 3) | ((d.y < 0.f) << 4) |
-          ((d.z < 0.f) << 5);
-  }
-
-  __device__ void begin_shadow(const ff3& o, float3 w) {
-    ftab(0) = ff_float(o.x); ftab(1) = ff_float(o.y); ftab(2) = ff_float(o.z);
-    ftab(3) = __fdiv_rn(1.0f, w.x);
-    ftab(4) = __fdiv_rn(1.0f, w.y);
-    ftab(5) = __fdiv_rn(1.0f, w.z);
-    dir = (w.x > 0.f) | ((w.y > 0.f) << 1) | ((w.z > 0.f) << 2) | ((w.x < 0.f) << 3) | ((w.y < 0.f) << 4) |
-          ((w.z < 0.f) << 5);
+    ftab(3) = inv[0]; ftab(4) = inv[1]; ftab(5) = inv[2];
+    dir = (int)bits;
   }
 
   __device__ __forceinline__ float density() const {
     return __ldg(P.rho + ((size_t)iz * P.ny + iy) * P.nx + ix);
   }
 
-  // exit parameter of axis a from the wall itself: ((i_a + [d_a > 0]) / n - o_a) / d_a, with the
-  // origin as a float-float pair in free flights
-  __device__ __forceinline__ float wall_free(int a, int i) const {
-    if (!((dir >> a) & 9)) return INFINITY;
+  // exit parameter of axis a from the wall itself, ((i_a + [d_a > 0]) / n - o_a) / d_a,
+  // with the origin as a float-float pair
+  __device__ __forceinline__ float wall(int a, int i) const {
     const float w = (float)(i + ((dir >> a) & 1)) * P.inv_n;     // exact
-    const float2 o = *reinterpret_cast<const float2*>(tab + a * EST_BLOCK);
-    return __fsub_rn(__fsub_rn(w, o.x), o.y) * ftab(3 + a);
-  }
-  __device__ __forceinline__ float wall_f(int a, int i) const {
-    if (!((dir >> a) & 9)) return INFINITY;
-    const float w = (float)(i + ((dir >> a) & 1)) * P.inv_n;
-    return (w - ftab(a)) * ftab(3 + a);
+    const float2 o = pair(a);
+    const float t = __fmul_rn(__fsub_rn(__fsub_rn(w, o.x), o.y), ftab(3 + a));
+    return ((dir >> a) & 9) ? t : INFINITY;
   }
 
-  __device__ __forceinline__ Hop hop_free(float t) {
-    const float tx = wall_free(0, ix), ty = wall_free(1, iy), tz = wall_free(2, iz);
+  __device__ __forceinline__ Hop hop(float t) {
+    const float tx = wall(0, ix), ty = wall(1, iy), tz = wall(2, iz);
     float best = tx;
-    axis = 0;
-    if (ty < best) { best = ty; axis = 1; }
-    if (tz < best) { best = tz; axis = 2; }
-    Hop h;
-    h.ok = best < INFINITY;
-    h.texit = fmaxf(best, t);
-    h.rho = density();
-    return h;
-  }
-
-  __device__ __forceinline__ Hop hop_shadow(float t) {
-    const float tx = wall_f(0, ix), ty = wall_f(1, iy), tz = wall_f(2, iz);
-    float best = tx;
-    axis = 0;
-    if (ty < best) { best = ty; axis = 1; }
-    if (tz < best) { best = tz; axis = 2; }
+    int ax = 0;
+    ax = ty < best ? 1 : ax;
+    best = fminf(best, ty);
+    ax = tz < best ? 2 : ax;
+    best = fminf(best, tz);
+    axis = ax;
     Hop h;
     h.ok = best < INFINITY;
     h.texit = fmaxf(best, t);
