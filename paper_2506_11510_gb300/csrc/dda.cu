@@ -41,8 +41,8 @@ static EstParams dda_est(const tg_camera& cam, const tg_medium& med, uint64_t se
   ep.cam = camera_setup(cam, box_min, cube);
   ep.med = medium_setup(med, cube);
   ep.seed = seed;
-  ep.regen_min = 8;
-  ep.ev_min = 8;
+  ep.regen_min = TV_REGEN_MIN;
+  ep.ev_min = TV_EV_MIN;
   return ep;
 }
 

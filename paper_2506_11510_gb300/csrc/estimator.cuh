@@ -45,6 +45,15 @@
 namespace tv {
 
 constexpr int EST_BLOCK = 256;
+#ifndef TV_EST_MIN_BLOCKS
+#define TV_EST_MIN_BLOCKS 4             // resident blocks per SM the register budget is sized for
+#endif
+#ifndef TV_REGEN_MIN
+#define TV_REGEN_MIN 8                  // idle lanes before a warp fetches new paths
+#endif
+#ifndef TV_EV_MIN
+#define TV_EV_MIN 16                    // waiting lanes before a warp handles events
+#endif
 constexpr int SEG_STEP_LIMIT = 1 << 20;      // cells per segment before a walk gives up
 // A shadow walk whose optical depth passes this value contributes at most
 // E * beta * p * e^-40 < 1e-16 and is stopped early (not in trace mode).
@@ -108,7 +117,8 @@ __device__ __forceinline__ bool box_intersect(const int C[3], float3 o, float3 d
 }
 
 template <class Walker, bool TRACE>
-__global__ void __launch_bounds__(EST_BLOCK) k_estimate(const typename Walker::Params wp, const EstParams ep) {
+__global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const typename Walker::Params wp,
+                                                                          const EstParams ep) {
   extern __shared__ double smem_d[];
   __shared__ float sun_inv[Walker::NDIR];
   __shared__ uint32_t sun_mask;

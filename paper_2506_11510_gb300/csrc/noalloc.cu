@@ -95,8 +95,8 @@ extern "C" int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const 
     ep.cam = camera_setup(*cam, G.box_min, G.cube);
     ep.med = medium_setup(*med, G.cube);
     ep.seed = seed;
-    ep.regen_min = 8;
-    ep.ev_min = 8;
+    ep.regen_min = TV_REGEN_MIN;
+    ep.ev_min = TV_EV_MIN;
     ep.spp = 1;
     ep.total = n;
     ep.counter = counter;

@@ -101,8 +101,8 @@ static EstParams est_params(const GridImpl& g, const tg_camera& cam, const tg_me
   ep.cam = camera_setup(cam, g.box_min, g.cube);
   ep.med = medium_setup(med, g.cube);
   ep.seed = seed;
-  ep.regen_min = 8;
-  ep.ev_min = 8;
+  ep.regen_min = TV_REGEN_MIN;
+  ep.ev_min = TV_EV_MIN;
   return ep;
 }
 
