@@ -33,8 +33,8 @@
 // Walker interface (tetrahedra: walk_tet.cuh, voxels: walk_voxel.cuh):
 //   bool intersect(o, d, &t_in)   slab test with the domain box (fp32)
 //   bool locate(p)                current cell := the cell that holds p
-//   void dir_table(d, inv, &m)    direction table of a segment (NDIR floats + mask)
-//   void begin(o, inv, m)         per-thread segment table for the ray o + t d
+//   void dir_table(d, inv)        direction table of a segment (NDIR floats)
+//   void begin(o, inv)            per-thread segment table for the ray o + t d
 //   Hop  hop(t)                   exit parameter of the current cell from t
 //   bool advance()                move to the pending cell (false: boundary)
 //   int  save() / restore(c)      remember / return to a cell
@@ -53,6 +53,12 @@ constexpr int EST_BLOCK = 256;
 #endif
 #ifndef TV_EV_MIN
 #define TV_EV_MIN 16                    // waiting lanes before a warp handles events
+#endif
+#ifndef TV_TILE
+#define TV_TILE 64                      // pixels are handed out in TV_TILE x TV_TILE tiles (when they divide the image)
+#endif
+#ifndef TV_STEPS_PER_ROUND
+#define TV_STEPS_PER_ROUND 4            // cell steps between two warp-wide regeneration / event rounds
 #endif
 constexpr int SEG_STEP_LIMIT = 1 << 20;      // cells per segment before a walk gives up
 // A shadow walk whose optical depth passes this value contributes at most
@@ -121,21 +127,17 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
                                                                           const EstParams ep) {
   extern __shared__ double smem_d[];
   __shared__ float sun_inv[Walker::NDIR];
-  __shared__ uint32_t sun_mask;
   Walker W(wp, smem_d);
   const MedF& M = ep.med;
   if (threadIdx.x == 0) {
     const ff3 w = {ff_make(M.sun_w[0]), ff_make(M.sun_w[1]), ff_make(M.sun_w[2])};
     float inv[Walker::NDIR];
-    uint32_t m;
-    W.dir_table(w, inv, &m);
+    W.dir_table(w, inv);
     for (int i = 0; i < Walker::NDIR; ++i) sun_inv[i] = inv[i];
-    sun_mask = m;
   }
   __syncthreads();
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
-  const ff sig_unit = ff{M.sig_hi, M.sig_lo};
 
   int state = S_IDLE, mode = M_FREE, ev = 0;
   long long pid = 0;
@@ -175,9 +177,8 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
   // a free flight from o along d: SampleFreePath gives the optical depth to consume
   auto start_free = [&](int b) {
     float inv[Walker::NDIR];
-    uint32_t m;
-    W.dir_table(d, inv, &m);
-    W.begin(o, inv, m);
+    W.dir_table(d, inv);
+    W.begin(o, inv);
     t = 0.f;
     acc = ff_make(0.f);
     lim = -logf(1.0f - rng_u(ep.seed, pixel, sample, 2 + 3 * b));
@@ -205,10 +206,20 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           if (TRACE) {
             px = ep.px[pid]; py = ep.py[pid]; s = ep.ps[pid];
           } else {
+            // all samples of a pixel together; pixels tile by tile (row-major tiles), which keeps the
+            // cells the warps in flight touch close together
             const long long pix = pid / ep.spp;
             s = ep.sample_offset + (int)(pid - pix * ep.spp);
-            px = (int)(pix % ep.cam.W);
-            py = (int)(pix / ep.cam.W);
+            if (TV_TILE > 1 && ep.cam.W % TV_TILE == 0 && ep.cam.H % TV_TILE == 0) {
+              const long long tile = pix / (TV_TILE * TV_TILE);
+              const int in = (int)(pix - tile * (TV_TILE * TV_TILE));
+              const int tpr = ep.cam.W / TV_TILE;
+              px = (int)(tile % tpr) * TV_TILE + in % TV_TILE;
+              py = (int)(tile / tpr) * TV_TILE + in / TV_TILE;
+            } else {
+              px = (int)(pix % ep.cam.W);
+              py = (int)(pix / ep.cam.W);
+            }
           }
           pixel = (uint32_t)(py * ep.cam.W + px);
           sample = (uint32_t)s;
@@ -258,7 +269,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           ++ncoll; ++c_coll;
           record(-1);
           saved = W.save();
-          W.begin(o, sun_inv, sun_mask);
+          W.begin(o, sun_inv);
           t = 0.f;
           acc = ff_make(0.f);
           lim = TRACE ? INFINITY : SHADOW_TAU_CUTOFF;
@@ -291,33 +302,36 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       }
     }
     if (__all_sync(~0u, state == S_DONE)) break;
-    if (state != S_WALK) continue;
 
-    // ---- one cell: ReadDensity and MarchThroughCells (or the shadow walk) ----
-    record(W.cell());
-    ++seg_steps;
-    if (TRACE) ++psteps;
-    const Hop h = W.hop(t);
-    if (!h.ok) { flags |= 16; finish(); continue; }
-    if (mode == M_FREE) ++c_steps; else ++c_shadow;
-    const ff sig = ff_mul_f(sig_unit, h.rho);
-    const ff dtau = ff_mul_f(sig, h.texit - t);
-    const ff sum = ff_add_fast(acc, dtau);
-    if (h.rho > 0.f && !ff_lt(sum, ff_make(lim))) {
-      // the segment's optical-depth limit falls inside this cell
-      if (mode == M_FREE) acc = ff_add(ff_make(t), ff_div(ff_sub(ff_make(lim), acc), sig));
-      ev = EV_LIMIT;
-      state = S_EVENT;
-      continue;
-    }
-    acc = sum;
-    t = h.texit;
-    if (!W.advance()) {
-      ev = EV_BOUNDARY;
-      state = S_EVENT;
-    } else if (seg_steps >= SEG_STEP_LIMIT) {
-      flags |= 8; ++c_lim;
-      finish();
+    // ---- cells: ReadDensity and MarchThroughCells (or the shadow walk) ----
+#pragma unroll 1
+    for (int k = 0; k < TV_STEPS_PER_ROUND && state == S_WALK; ++k) {
+      record(W.cell());
+      ++seg_steps;
+      if (TRACE) ++psteps;
+      const Hop h = W.hop(t);
+      if (!h.ok) { flags |= 16; finish(); break; }
+      if (mode == M_FREE) ++c_steps; else ++c_shadow;
+      // optical depth of the cell: (sigma_unit * rho) * (t_exit - t), the product kept exactly
+      const ff sig = two_prod(M.sig_hi, h.rho);
+      const ff dtau = ff_mul_f(sig, h.texit - t);
+      const ff sum = ff_add_fast(acc, dtau);
+      if (h.rho > 0.f && !ff_lt(sum, ff_make(lim))) {
+        // the segment's optical-depth limit falls inside this cell
+        if (mode == M_FREE) acc = ff_add(ff_make(t), ff_div(ff_sub(ff_make(lim), acc), sig));
+        ev = EV_LIMIT;
+        state = S_EVENT;
+        break;
+      }
+      acc = sum;
+      t = h.texit;
+      if (!W.advance()) {
+        ev = EV_BOUNDARY;
+        state = S_EVENT;
+      } else if (seg_steps >= SEG_STEP_LIMIT) {
+        flags |= 8; ++c_lim;
+        finish();
+      }
     }
   }
 

@@ -130,9 +130,8 @@ __global__ void __launch_bounds__(EST_BLOCK) k_optical_depth(const TetParams P, 
                    ff_add(ff_make(o.z), two_prod(tin, d.z))};
     if (W.locate(make_float3(ff_float(e.x), ff_float(e.y), ff_float(e.z)))) {
       float tinv[TetWalker<FMT>::NDIR];
-      uint32_t m;
-      W.dir_table(ff3{ff_make(d.x), ff_make(d.y), ff_make(d.z)}, tinv, &m);
-      W.begin(e, tinv, m);
+      W.dir_table(ff3{ff_make(d.x), ff_make(d.y), ff_make(d.z)}, tinv);
+      W.begin(e, tinv);
       float t = 0.f;
       for (; k < SEG_STEP_LIMIT; ++k) {
         if (seq && len < seq_cap) seq[i * seq_cap + len] = W.cell();

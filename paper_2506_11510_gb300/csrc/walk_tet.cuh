@@ -7,8 +7,9 @@
 // x+z, x-z}, so per segment the walker keeps, for each orientation p,
 // nO[p] = (P[p] . o) 2^K and invND[p] = 2^-K / (P[p] . d) in shared memory
 // (one column per thread: conflict-free), and the exit parameter of a face with
-// integer plane offset c (units of 2^-K) is (c - nO[p]) * invND[p].  A 32-bit
-// mask marks the orientation ids p | s << 4 whose outward normal points along d.
+// integer plane offset c (units of 2^-K) is (c - nO[p]) * invND[p].  The
+// reciprocals are stored per orientation id p | s << 4, NaN where the outward
+// normal does not point along d (a face that cannot be an exit).
 // Free flights keep nO as a float-float pair (hi, lo), so that c - nO is
 // accurate to the distance walked rather than to |o|; shadow walks keep it as
 // one float.  Both use the same per-thread 8-byte slots.
@@ -126,38 +127,50 @@ inline __device__ long long tet_locate(const TetParams& P, float3 p) {
   return lo - 1;
 }
 
-// Orientation table of a direction: invND[p] = 2^-K / (P[p] . d) (the reciprocal
-// is correctly rounded and 2^-K exact) and the mask of orientation ids p | s << 4
-// whose outward normal points along d.
-__device__ __forceinline__ void tet_dir_table(const ff3& d, float invK, float inv[9], uint32_t* mask) {
+// Orientation table of a direction, indexed by the orientation id p | s << 4:
+// 2^-K / (P[p] . d) (correctly rounded reciprocal, exact scaling) when the
+// outward normal (-1)^s P[p] points along d, NaN otherwise -- a NaN exit
+// parameter never compares smaller, so masked faces need no test.
+constexpr int TET_NID = 25;
+
+__device__ __forceinline__ void tet_dir_table(const ff3& d, float invK, float inv[TET_NID]) {
   const float nd[9] = {ff_float(d.x), ff_float(d.y), ff_float(d.z), ff_float(ff_add(d.x, d.y)),
                        ff_float(ff_sub(d.x, d.y)), ff_float(ff_add(d.y, d.z)), ff_float(ff_sub(d.y, d.z)),
                        ff_float(ff_add(d.x, d.z)), ff_float(ff_sub(d.x, d.z))};
-  uint32_t m = 0;
+#pragma unroll
+  for (int q = 0; q < TET_NID; ++q) inv[q] = __int_as_float(0x7FFFFFFF);
 #pragma unroll
   for (int p = 0; p < 9; ++p) {
-    inv[p] = __frcp_rn(nd[p]) * invK;
-    m |= (nd[p] > 0.f ? 1u : 0u) << p;
-    m |= (nd[p] < 0.f ? 1u : 0u) << (p + 16);
+    const float r = __frcp_rn(nd[p]) * invK;
+    if (nd[p] > 0.f) inv[p] = r;
+    if (nd[p] < 0.f) inv[p | 16] = r;
   }
-  *mask = m;
 }
+
+#ifndef TV_PREFETCH
+#define TV_PREFETCH 0                   // load the next cell's record as soon as the exit face is known
+#endif
 
 template <int FMT>
 struct TetWalker {
   using Params = TetParams;
-  static constexpr int NDIR = 9;            // direction-table entries
+  static constexpr int NDIR = TET_NID;      // direction-table entries
   const TetParams& P;
-  double* tab;         // this thread's column: slot q at tab[q * EST_BLOCK], 18 slots
-  uint32_t mask;
+  double* tab;         // this thread's column: nO pair p at tab[p * EST_BLOCK] (9 slots), then the
+                       // direction table as floats, entry q at ((float*)(tab0 + 9 EST_BLOCK))[q * EST_BLOCK]
+  float* itab;
   int cur, nxt;
+#if TV_PREFETCH
+  uint4 ra, rb;        // record of the current cell
+  uint4 na, nb;        // record of the pending next cell, in flight
+#endif
 
-  static size_t smem_bytes() { return sizeof(double) * 18 * EST_BLOCK; }
+  static size_t smem_bytes() { return (sizeof(double) * 9 + sizeof(float) * TET_NID) * EST_BLOCK; }
 
-  __device__ TetWalker(const TetParams& p, double* smem) : P(p), tab(smem + threadIdx.x), mask(0), cur(0), nxt(0) {}
+  __device__ TetWalker(const TetParams& p, double* smem)
+      : P(p), tab(smem + threadIdx.x), itab(reinterpret_cast<float*>(smem + 9 * EST_BLOCK) + threadIdx.x), cur(0),
+        nxt(0) {}
 
-  __device__ __forceinline__ float& ftab(int q) { return *reinterpret_cast<float*>(tab + q * EST_BLOCK); }
-  __device__ __forceinline__ float ftab(int q) const { return *reinterpret_cast<const float*>(tab + q * EST_BLOCK); }
   __device__ __forceinline__ float2& pair(int q) { return *reinterpret_cast<float2*>(tab + q * EST_BLOCK); }
   __device__ __forceinline__ float2 pair(int q) const { return *reinterpret_cast<const float2*>(tab + q * EST_BLOCK); }
 
@@ -166,24 +179,23 @@ struct TetWalker {
   __device__ bool locate(float3 p) {
     const long long c = tet_locate(P, p);
     cur = (int)c;
+#if TV_PREFETCH
+    if (c >= 0) load(ra, rb);
+#endif
     return c >= 0;
   }
 
-  __device__ __forceinline__ void dir_table(const ff3& d, float inv[9], uint32_t* m) const {
-    tet_dir_table(d, P.invK, inv, m);
-  }
+  __device__ __forceinline__ void dir_table(const ff3& d, float inv[TET_NID]) const { tet_dir_table(d, P.invK, inv); }
 
   // Per-segment table: nO[p] = (P[p] . o) 2^K as a float-float pair (so c - nO is
   // accurate to the distance walked, not to |o|), and the direction table.
-  __device__ void begin(const ff3& o, const float inv[9], uint32_t m) {
+  __device__ void begin(const ff3& o, const float* inv) {
     const ff no[9] = {o.x, o.y, o.z, ff_add(o.x, o.y), ff_sub(o.x, o.y), ff_add(o.y, o.z), ff_sub(o.y, o.z),
                       ff_add(o.x, o.z), ff_sub(o.x, o.z)};
 #pragma unroll
-    for (int p = 0; p < 9; ++p) {
-      pair(p) = make_float2(no[p].hi * P.scaleK, no[p].lo * P.scaleK);
-      ftab(9 + p) = inv[p];
-    }
-    mask = m;
+    for (int p = 0; p < 9; ++p) pair(p) = make_float2(no[p].hi * P.scaleK, no[p].lo * P.scaleK);
+#pragma unroll
+    for (int q = 0; q < TET_NID; ++q) itab[q * EST_BLOCK] = inv[q];
   }
 
   __device__ __forceinline__ void load(uint4& a, uint4& b) const {
@@ -191,12 +203,16 @@ struct TetWalker {
     b = __ldg(P.rec + 2 * (size_t)cur + 1);
   }
 
-  // Exit of the current cell from parameter t.  All four faces are evaluated and
-  // the ones whose outward normal does not face the ray are masked out, so the
-  // lanes of a warp execute one instruction stream.
+  // Exit of the current cell from parameter t.  All four faces are evaluated; the
+  // ones whose outward normal does not face the ray get a NaN parameter from the
+  // direction table and never win, so the lanes of a warp run one instruction stream.
   __device__ __forceinline__ Hop hop(float t) {
+#if TV_PREFETCH
+    const uint4 a = ra, b = rb;
+#else
     uint4 a, b;
     load(a, b);
+#endif
     const uint32_t link[4] = {a.x, a.y, a.z, a.w};
     const int c[4] = {sext24(b.x), sext24((b.x >> 24) | (b.y << 8)), sext24((b.y >> 16) | (b.z << 16)),
                       sext24(b.z >> 8)};
@@ -205,15 +221,19 @@ struct TetWalker {
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const uint32_t id = link[f] >> 27;
-      const int p = (int)(id & 15u);
-      const float2 no = pair(p);
-      float tf = __fmul_rn(__fsub_rn(__fsub_rn((float)c[f], no.x), no.y), ftab(9 + p));
-      tf = ((mask >> id) & 1u) ? tf : INFINITY;
+      const float2 no = pair((int)(id & 15u));
+      const float tf = __fmul_rn(__fsub_rn(__fsub_rn((float)c[f], no.x), no.y), itab[id * EST_BLOCK]);
       const bool better = tf < best;
       best = better ? tf : best;
       blink = better ? link[f] : blink;
     }
     nxt = (int)(blink & NO_NBR);
+#if TV_PREFETCH
+    if ((uint32_t)nxt != NO_NBR) {
+      na = __ldg(P.rec + 2 * (size_t)nxt);
+      nb = __ldg(P.rec + 2 * (size_t)nxt + 1);
+    }
+#endif
     Hop h;
     h.ok = best < INFINITY;
     h.texit = fmaxf(best, t);
@@ -224,10 +244,19 @@ struct TetWalker {
   __device__ __forceinline__ bool advance() {
     if ((uint32_t)nxt == NO_NBR) return false;
     cur = nxt;
+#if TV_PREFETCH
+    ra = na;
+    rb = nb;
+#endif
     return true;
   }
   __device__ __forceinline__ int save() const { return cur; }
-  __device__ __forceinline__ void restore(int c) { cur = c; }
+  __device__ __forceinline__ void restore(int c) {
+    cur = c;
+#if TV_PREFETCH
+    load(ra, rb);
+#endif
+  }
   __device__ __forceinline__ int cell() const { return cur; }
 };
 

@@ -17,7 +17,7 @@ struct VoxParams {
 
 struct VoxelWalker {
   using Params = VoxParams;
-  static constexpr int NDIR = 4;            // direction-table entries: 1/d.x, 1/d.y, 1/d.z, sign bits
+  static constexpr int NDIR = 4;            // direction-table entries: 1/d.x, 1/d.y, 1/d.z (NaN if 0), sign bits
   const VoxParams& P;
   double* tab;        // 8-byte slots: o.x, o.y, o.z as float-float pairs, then 1/d.x, 1/d.y, 1/d.z
   int ix, iy, iz;
@@ -49,25 +49,24 @@ struct VoxelWalker {
     return true;
   }
 
-  __device__ __forceinline__ void dir_table(const ff3& dd, float inv[4], uint32_t* m) const {
+  __device__ __forceinline__ void dir_table(const ff3& dd, float inv[4]) const {
     const float d[3] = {ff_float(dd.x), ff_float(dd.y), ff_float(dd.z)};
     uint32_t bits = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      inv[a] = d[a] != 0.f ? __frcp_rn(d[a]) : INFINITY;
+      inv[a] = d[a] != 0.f ? __frcp_rn(d[a]) : __int_as_float(0x7FFFFFFF);
       bits |= (d[a] > 0.f ? 1u : 0u) << a;
       bits |= (d[a] < 0.f ? 1u : 0u) << (3 + a);
     }
-    inv[3] = 0.f;
-    *m = bits;
+    inv[3] = __int_as_float((int)bits);
   }
 
-  __device__ void begin(const ff3& o, const float inv[4], uint32_t bits) {
+  __device__ void begin(const ff3& o, const float* inv) {
     pair(0) = make_float2(o.x.hi, o.x.lo);
     pair(1) = make_float2(o.y.hi, o.y.lo);
     pair(2) = make_float2(o.z.hi, o.z.lo);
     ftab(3) = inv[0]; ftab(4) = inv[1]; ftab(5) = inv[2];
-    dir = (int)bits;
+    dir = __float_as_int(inv[3]);
   }
 
   __device__ __forceinline__ float density() const {
@@ -79,18 +78,16 @@ struct VoxelWalker {
   __device__ __forceinline__ float wall(int a, int i) const {
     const float w = (float)(i + ((dir >> a) & 1)) * P.inv_n;     // exact
     const float2 o = pair(a);
-    const float t = __fmul_rn(__fsub_rn(__fsub_rn(w, o.x), o.y), ftab(3 + a));
-    return ((dir >> a) & 9) ? t : INFINITY;
+    return __fmul_rn(__fsub_rn(__fsub_rn(w, o.x), o.y), ftab(3 + a));   // NaN when d_a = 0
   }
 
   __device__ __forceinline__ Hop hop(float t) {
     const float tx = wall(0, ix), ty = wall(1, iy), tz = wall(2, iz);
-    float best = tx;
+    float best = INFINITY;
     int ax = 0;
-    ax = ty < best ? 1 : ax;
-    best = fminf(best, ty);
-    ax = tz < best ? 2 : ax;
-    best = fminf(best, tz);
+    if (tx < best) { best = tx; ax = 0; }
+    if (ty < best) { best = ty; ax = 1; }
+    if (tz < best) { best = tz; ax = 2; }
     axis = ax;
     Hop h;
     h.ok = best < INFINITY;
