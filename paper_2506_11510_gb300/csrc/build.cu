@@ -805,6 +805,8 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   G.qmin = mn.release();
   G.qmax = mx.release();
   G.scratch = scratch.release();
+  build_locator(G, st);
+  TV_CUDA(cudaStreamSynchronize(st));
   return TG_OK;
 }
 

@@ -78,8 +78,13 @@ struct GridImpl {
   unsigned long long* sum = nullptr;
   float* majorant = nullptr;
   unsigned long long* scratch = nullptr; // work counter of the persistent renderer
+  int32_t* locator = nullptr;            // cell of each locator-grid cell centre (loc_R per cube edge)
+  int loc_R = 0;
   ~GridImpl();
 };
+
+// Builds G.locator (point-location accelerator) for a finished grid.
+void build_locator(GridImpl& G, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 multiplies

@@ -162,6 +162,8 @@ int tg_grid_import(const tg_volume_desc* vol, int32_t K, int64_t num_tets, const
     G.rec = rec.release();
     G.codes = cd.release();
     G.scratch = scratch.release();
+    build_locator(G, st);
+    TV_CUDA(cudaStreamSynchronize(st));
   } catch (const Error& e) {
     delete g;
     return e.code;

@@ -107,6 +107,8 @@ extern "C" int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const 
     for (int a = 0; a < 3; ++a) p.C[a] = G.C[a];
     p.scaleK = std::ldexp(1.0f, G.K);
     p.invK = std::ldexp(1.0f, -G.K);
+    p.locator = G.locator;
+    p.R = G.loc_R;
     switch (G.fmt) {
       case TG_DENSITY_BF16: launch_estimate<TetWalker<TG_DENSITY_BF16>, true>(p, ep, st); break;
       case TG_DENSITY_FP16: launch_estimate<TetWalker<TG_DENSITY_FP16>, true>(p, ep, st); break;

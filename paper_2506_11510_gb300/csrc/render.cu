@@ -10,7 +10,7 @@ GridImpl::~GridImpl() {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch};
+  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (prev >= 0) cudaSetDevice(prev);
@@ -82,7 +82,35 @@ static TetParams tet_params(const GridImpl& g) {
   for (int a = 0; a < 3; ++a) p.C[a] = g.C[a];
   p.scaleK = std::ldexp(1.0f, g.K);
   p.invK = std::ldexp(1.0f, -g.K);
+  p.locator = g.locator;
+  p.R = g.loc_R;
   return p;
+}
+
+__global__ void k_locator(TetParams P, int32_t* out, int nx, int ny, int nz) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nx * ny * nz) return;
+  const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+  const float h = 1.0f / (float)P.R;
+  const long long c = tet_locate(P, make_float3(((float)x + 0.5f) * h, ((float)y + 0.5f) * h, ((float)z + 0.5f) * h));
+  out[i] = (int32_t)c;
+}
+
+void build_locator(GridImpl& G, cudaStream_t st) {
+  if (G.n == 0) return;
+  // about one locator cell per 4 tetrahedra, a power of two per cube edge in [8, 256]
+  const double cubes = (double)G.C[0] * G.C[1] * G.C[2];
+  int R = 8;
+  while (R < 256 && (double)(2 * R) * (2 * R) * (2 * R) * cubes <= (double)G.n / 4.0) R *= 2;
+  const long long nx = (long long)G.C[0] * R, ny = (long long)G.C[1] * R, nz = (long long)G.C[2] * R;
+  DevBuf<int32_t> loc((size_t)(nx * ny * nz));
+  TetParams p = tet_params(G);
+  p.locator = nullptr;
+  p.R = R;
+  k_locator<<<(unsigned)((nx * ny * nz + 255) / 256), 256, 0, st>>>(p, loc.p, (int)nx, (int)ny, (int)nz);
+  TV_LAUNCH();
+  G.locator = loc.release();
+  G.loc_R = R;
 }
 
 template <bool TRACE>

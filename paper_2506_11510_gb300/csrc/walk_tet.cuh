@@ -25,6 +25,8 @@ struct TetParams {
   int K, depth;                 // vertex scale exponent; deepest level present
   int C[3];                     // cubes per axis
   float scaleK, invK;           // 2^K, 2^-K
+  const int32_t* locator;       // cell holding the centre of each locator-grid cell (may be null)
+  int R;                        // locator cells per cube edge
 };
 
 __device__ __forceinline__ int sext24(uint32_t v) { return ((int)(v << 8)) >> 8; }
@@ -176,8 +178,48 @@ struct TetWalker {
 
   __device__ bool intersect(float3 o, float3 d, float* t_in) const { return box_intersect(P.C, o, d, t_in); }
 
+  // Point location: start from the cell that holds the centre of p's locator-grid
+  // cell and walk the straight segment from that centre to p; where the segment
+  // ends, the current cell holds p.  Near the domain boundary (camera-ray entry
+  // points) cells are coarse and this takes a step or two.  Falls back to the
+  // exact descent of the LEB hierarchy.
   __device__ bool locate(float3 p) {
-    const long long c = tet_locate(P, p);
+    long long c = -1;
+    if (P.locator) {
+      const float pc[3] = {p.x, p.y, p.z};
+      int idx[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int lim = P.C[a] * P.R - 1;
+        const int v = (int)floorf(pc[a] * (float)P.R);
+        idx[a] = v < 0 ? 0 : (v > lim ? lim : v);
+      }
+      const int start = P.locator[((size_t)idx[2] * (P.C[1] * P.R) + idx[1]) * (P.C[0] * P.R) + idx[0]];
+      if (start >= 0) {
+        const float h = 1.0f / (float)P.R;
+        const float3 ctr = make_float3(((float)idx[0] + 0.5f) * h, ((float)idx[1] + 0.5f) * h,
+                                       ((float)idx[2] + 0.5f) * h);
+        const float3 v = make_float3(p.x - ctr.x, p.y - ctr.y, p.z - ctr.z);
+        const float len = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+        cur = start;
+        c = start;
+        if (len > 0.f) {
+          const float inv = 1.0f / len;
+          float tinv[TET_NID];
+          dir_table(ff3{ff_make(v.x * inv), ff_make(v.y * inv), ff_make(v.z * inv)}, tinv);
+          begin(ff3{ff_make(ctr.x), ff_make(ctr.y), ff_make(ctr.z)}, tinv);
+          float t = 0.f;
+          int k = 0;
+          for (; k < 64; ++k) {
+            const Hop hp = hop(t);
+            if (!hp.ok || hp.texit >= len || !advance()) break;
+            t = hp.texit;
+          }
+          c = k == 64 ? -1 : cur;
+        }
+      }
+    }
+    if (c < 0) c = tet_locate(P, p);
     cur = (int)c;
 #if TV_PREFETCH
     if (c >= 0) load(ra, rb);
