@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--scene", default="production")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-dda", action="store_true", help="skip the regular-grid comparator frame")
     p.add_argument("--cpu-sample-px", type=int, default=0, help="side of the oracle's pixel window (0: auto)")
     return p.parse_args()
 
@@ -170,6 +171,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     build_ms = (time.time() - t0) * 1e3
     ntets = grid.info.num_tets
+    grid_depth = grid.info.max_depth
 
     W_, H_ = s.camera.width, s.camera.height
     img = torch.zeros((H_, W_), dtype=torch.float32, device=dev)
@@ -215,6 +217,24 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     paths = float(W_ * H_ * spp)
     value = paths * ws * args.steps / (total_ms * 1e-3) / 1e6
+
+    # the regular-grid comparator (3D DDA, same estimator) on the same volume, camera and medium
+    comparator = None
+    if not args.no_dda:
+        dsum = torch.zeros_like(img)
+        dst = tv.new_stats(dev)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        tv.grid_render(vol, s.box_min, s.voxel_size, s.camera, s.medium, spp, s.render_seed, offset, dsum, None, dst,
+                       want_sq=False)
+        a1.record(st)
+        torch.cuda.synchronize()
+        dda_ms = a0.elapsed_time(a1)
+        dcount = tv.stats_dict(dst)
+        comparator = {"method": "regular voxel grid, 3D DDA, same estimator", "voxels": int(vol.numel()),
+                      "ms_per_frame": round(dda_ms, 2), "mpaths_s": round(paths / dda_ms / 1e3, 3),
+                      "voxel_steps_per_path": round((dcount["tet_steps"] + dcount["shadow_steps"]) / paths, 1),
+                      "tet_speedup": round(dda_ms / (total_ms / args.steps), 3)}
 
     # end to end through the public API: host volume -> device, build, render, image -> host
     e2e = None
@@ -267,7 +287,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded procedural volume; stands in for the paper's OpenVDB assets)",
                 "config": {"workload": workload_name(s, ntets), "ms_per_frame": round(ms_per_step, 3),
-                           "tets": ntets, "grid_depth": grid_max_depth(ntets, s), "build_ms": round(build_ms, 1),
+                           "tets": ntets, "grid_depth": grid_depth, "build_ms": round(build_ms, 1),
                            "width": W_, "height": H_, "spp": spp, "paths_per_frame": int(paths),
                            "tet_steps_per_path": round(steps_per_frame / paths, 2),
                            "collisions_per_path": round(counters["collisions"] / paths, 3),
@@ -275,14 +295,10 @@ def run_ours(args):
                            "l2": "inputs larger than L2: grid records %.2f GB" % (ntets * 32 / 1e9),
                            "parallelism": "one frame per rank, disjoint sample ranges"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clk}
+                "clocks": clk, "comparator": comparator}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
-
-
-def grid_max_depth(ntets, s):
-    return None
 
 
 # ---------------------------------------------------------------------------
@@ -304,20 +320,29 @@ def oracle_window(s, vol_np, side, nthreads=0):
     return g, wcam, time.time() - t0
 
 
-def oracle_window_render(s, g, wcam, nthreads=0):
-    """All paths of the window at the frame's spp; returns (paths, seconds)."""
+def oracle_window_render(s, g, wcam, min_seconds=10.0, nthreads=0):
+    """The window's paths at the frame's spp, repeated over further sample ranges
+    until at least min_seconds have passed (at most 256 frames); returns (paths, seconds)."""
     import numpy as np
     side = wcam.width
     py, px, sm = np.meshgrid(np.arange(side), np.arange(side), np.arange(s.spp), indexing="ij")
+    px, py, sm = px.ravel(), py.ravel(), sm.ravel()
     t0 = time.time()
-    g.render_paths(wcam, s.medium, s.render_seed, px.ravel(), py.ravel(), sm.ravel(), nthreads=nthreads)
-    return side * side * s.spp, time.time() - t0
+    paths, k = 0, 0
+    while k < 256:
+        g.render_paths(wcam, s.medium, s.render_seed, px, py, sm + k * s.spp, nthreads=nthreads)
+        paths += len(px)
+        k += 1
+        if time.time() - t0 >= min_seconds:
+            break
+    return paths, time.time() - t0
 
 
 def cpu_sample_text(side, s, paths, tb):
-    return ("%dx%d-pixel window at the frame centre, %d spp (%d paths), on the oracle's grid refined for the "
-            "window's sub-frustum only (coarse elsewhere, so paths are cheaper than the full frame's; built once "
-            "in %.0f s, not timed); fp64 C++, OpenMP over paths" % (side, side, s.spp, paths, tb))
+    return ("%dx%d-pixel window at the frame centre, %d spp per frame, %d paths over successive sample ranges, "
+            "on the oracle's grid refined for the window's sub-frustum only (coarse elsewhere, so paths are "
+            "cheaper than the full frame's; built once in %.0f s, not timed); fp64 C++, OpenMP over paths"
+            % (side, side, s.spp, paths, tb))
 
 
 def cpu_baseline(args, s, vol):
@@ -345,13 +370,14 @@ def run_reference(args):
     side = args.cpu_sample_px or 64
     g, wcam, tb = oracle_window(s, vol, side)
     for _ in range(args.warmup):
-        oracle_window_render(s, g, wcam)
-    times, paths = [], 0
+        oracle_window_render(s, g, wcam, min_seconds=0.0)
+    times, counts = [], []
     for _ in range(max(1, args.steps)):
-        paths, tr = oracle_window_render(s, g, wcam)
+        paths, tr = oracle_window_render(s, g, wcam, min_seconds=5.0)
         times.append(tr)
+        counts.append(paths)
     mean = sum(times) / len(times)
-    value = paths / mean / 1e6
+    value = sum(counts) / sum(times) / 1e6
     cores = os.cpu_count() or 1
     line = {"metric": METRIC, "value": round(value, 5), "unit": "Mpaths/s", "n_gpus": ws, "steps": len(times),
             "warmup": args.warmup, "ms_per_step": round(mean * 1e3, 2), "higher_is_better": True,
