@@ -149,6 +149,10 @@ __device__ __forceinline__ void tet_dir_table(const ff3& d, float invK, float in
   }
 }
 
+#ifndef TV_LD256
+#define TV_LD256 0                      // fetch a 32-byte record with one 256-bit load
+#endif
+
 #ifndef TV_PREFETCH
 #define TV_PREFETCH 0                   // load the next cell's record as soon as the exit face is known
 #endif
@@ -241,8 +245,14 @@ struct TetWalker {
   }
 
   __device__ __forceinline__ void load(uint4& a, uint4& b) const {
+#if TV_LD256
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(P.rec + 2 * (size_t)cur));
+#else
     a = __ldg(P.rec + 2 * (size_t)cur);
     b = __ldg(P.rec + 2 * (size_t)cur + 1);
+#endif
   }
 
   // Exit of the current cell from parameter t.  All four faces are evaluated; the
