@@ -153,7 +153,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     import paper_2506_11510_gb300 as tv
-    from paper_2506_11510_gb300 import _build, workloads as W
+    from paper_2506_11510_gb300 import _build, sharding, workloads as W
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -178,7 +178,7 @@ def run_ours(args):
     img2 = torch.zeros_like(img)
     stats = tv.new_stats(dev)
     spp = s.spp
-    offset = rank * spp                                   # each rank its own samples
+    offset, _ = sharding.sample_range(rank, ws, spp)      # each rank its own samples
 
     for _ in range(args.warmup):
         tv.tet_render(grid, s.camera, s.medium, spp, s.render_seed, offset, img, img2)
