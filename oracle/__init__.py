@@ -178,6 +178,20 @@ class Grid:
             out.update(seq=seq, seq_len=seq_len)
         return out
 
+    def cache_paths(self, camera, medium, seed, px, py, sample, cache_depth=0, max_vertices=0, nthreads=0):
+        """The radiance cache's uses of the tracer: cached-path records (cache_depth > 0,
+        query [n][8]) and training samples from path vertices (vertices [n][max_vertices][8])."""
+        px = np.ascontiguousarray(px, np.int32); py = np.ascontiguousarray(py, np.int32)
+        sm = np.ascontiguousarray(sample, np.int32)
+        n = len(px)
+        q = np.zeros((n, 8), np.float64) if cache_depth > 0 else None
+        v = np.zeros((n, max_vertices, 8), np.float64) if max_vertices > 0 else None
+        L = np.empty(n, np.float64); flags = np.empty(n, np.int32)
+        _check(lib().orc_cache_paths(self._h, C.byref(camera_struct(camera)), C.byref(medium_struct(medium)),
+                                     C.c_uint64(seed), C.c_int64(n), _p(px), _p(py), _p(sm), cache_depth, _p(q),
+                                     max_vertices, _p(v), _p(L), _p(flags), nthreads))
+        return dict(query=q, vertices=v, L=L, flags=flags)
+
     def render(self, camera, medium, spp, seed, sample_offset=0, nthreads=0):
         s = np.zeros((camera.height, camera.width), np.float64)
         s2 = np.zeros_like(s)

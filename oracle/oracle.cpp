@@ -826,6 +826,21 @@ Ray camera_ray(const CamRay& c, int px, int py, double u0, double u1) {
 
 struct PathOut { double L; int32_t flags, collisions; int64_t steps; int32_t seq_len; };
 
+// Learned radiance cache (the cached estimator): a path may end into the cache
+// at its depth-th collision, after that collision's next-event estimate; the
+// cache then stands for the rest of the path, the radiance that the scattered
+// continuation from x brings back along -d, weighted by the path throughput
+// after the albedo at x.  Training samples are a full path's own collision
+// vertices: position x (grid space divided by the domain extent, in [0,1]^3),
+// the direction d the path arrived with, and as target the rest of that path's
+// estimate, (L_final - L after vertex j's NEE) / beta_j.  Both use 8 doubles.
+struct CacheIO {
+  int depth = 0;               // > 0: end the path into the cache at this collision
+  double* query = nullptr;     // [8]: x (3), beta, d (3), L so far; beta = 0 when the path ended before
+  int vcap = 0;                // vertices recorded per path
+  double* vtx = nullptr;       // [vcap][8]: x (3), target, d (3), valid
+};
+
 // Sec. 3, Algorithm 1 "Trace", with the estimator around it: throughput beta
 // is multiplied by the albedo at every collision; every collision adds the sun
 // seen through the shadow ray (next-event estimation); a path that leaves the
@@ -833,8 +848,28 @@ struct PathOut { double L; int32_t flags, collisions; int64_t steps; int32_t seq
 template <class Cells, class Locate>
 PathOut trace(const Cells& cells, const Domain& D, const Locate& locate_fn, const CamRay& cr,
               const orc_medium* med, uint64_t seed, int px, int py, int sample,
-              int32_t* seq, int32_t seq_cap) {
+              int32_t* seq, int32_t seq_cap, CacheIO* cache = nullptr) {
   PathOut out = {0, 0, 0, 0, 0};
+  int nv = 0;                              // cache: vertices recorded
+  double vbeta[64], vL[64];                // their throughput and the estimate after their NEE
+  if (cache && cache->vcap > 64) cache->vcap = 64;
+  auto finish_cache = [&](double Lf) {
+    if (!cache) return;
+    if (cache->query) {
+      if (cache->query[3] == 0) for (int k = 0; k < 7; ++k) cache->query[k] = 0;
+      cache->query[7] = Lf;
+    }
+    for (int j = 0; j < cache->vcap; ++j) {
+      double* v = cache->vtx + 8 * j;
+      if (j < nv && vbeta[j] > 0) {
+        v[3] = (Lf - vL[j]) / vbeta[j];
+        v[7] = 1;
+      } else {
+        for (int k = 0; k < 8; ++k) v[k] = 0;
+      }
+    }
+  };
+  if (cache && cache->query) cache->query[3] = 0;
   PathLog log = {seq, seq_cap, 0, false, 0, 0};
   uint32_t pixel = (uint32_t)(py * cr.W + px);
   double u0 = uniform(seed, pixel, (uint32_t)sample, 0), u1 = uniform(seed, pixel, (uint32_t)sample, 1);
@@ -843,11 +878,11 @@ PathOut trace(const Cells& cells, const Domain& D, const Locate& locate_fn, cons
   V3 w_sun = normalize(mul(from_f(med->sun_dir), -1.0));
   double t_in;
   if (!intersect_grid(D, ray, &t_in)) {                      // "IntersectGrid"
-    out.L = med->env_radiance; out.flags = 4; return out;
+    out.L = med->env_radiance; out.flags = 4; finish_cache(out.L); return out;
   }
   ray.o = grid_intersection_point(ray, t_in);                // "GridIntersectionPoint"
   int32_t cell = locate_fn(ray.o);
-  if (cell < 0) { out.flags = 16; return out; }
+  if (cell < 0) { out.flags = 16; finish_cache(0); return out; }
   for (int b = 0;; ++b) {                                     // "while InsideGrid(ray)"
     double tau = sample_free_path(uniform(seed, pixel, sample, 2 + 3 * b));   // "SampleFreePath"
     V3 x;
@@ -865,12 +900,29 @@ PathOut trace(const Cells& cells, const Domain& D, const Locate& locate_fn, cons
     if (log.len < seq_cap) seq[log.len] = -1;
     log.len++;
     L += beta * hg_pdf(med->g, dot(ray.d, w_sun)) * med->sun_irradiance * T;
+    if (cache && nv < cache->vcap) {
+      double* v = cache->vtx + 8 * nv;
+      v[0] = x.x / D.C[0]; v[1] = x.y / D.C[1]; v[2] = x.z / D.C[2];
+      v[4] = ray.d.x; v[5] = ray.d.y; v[6] = ray.d.z;
+      vbeta[nv] = beta; vL[nv] = L;
+      ++nv;
+    }
     if (b + 1 >= med->max_bounces) { out.flags |= 2; break; }
+    if (cache && cache->depth > 0 && b + 1 == cache->depth) {
+      // the path ends into the cache: it stands for everything after this vertex
+      double* q = cache->query;
+      if (q) {
+        q[0] = x.x / D.C[0]; q[1] = x.y / D.C[1]; q[2] = x.z / D.C[2]; q[3] = beta;
+        q[4] = ray.d.x; q[5] = ray.d.y; q[6] = ray.d.z;
+      }
+      break;
+    }
     ray.d = sample_phase_function(med->g, uniform(seed, pixel, sample, 3 + 3 * b),
                                   uniform(seed, pixel, sample, 4 + 3 * b), ray.d);   // "SamplePhaseFunction"
     ray.o = x;
   }
   out.L = L;
+  finish_cache(L);
   if (log.degenerate) out.flags |= 1;
   out.steps = log.steps;
   out.seq_len = std::min(log.len, seq_cap);
@@ -970,6 +1022,31 @@ int orc_render_paths(const orc_grid* g, const orc_camera* cam, const orc_medium*
     if (collisions) collisions[i] = o.collisions;
     if (steps) steps[i] = o.steps;
     if (seq_len) seq_len[i] = o.seq_len;
+  }
+  return OK;
+}
+
+int orc_cache_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* med, uint64_t seed, int64_t n,
+                    const int32_t* px, const int32_t* py, const int32_t* sample, int32_t cache_depth,
+                    double* query, int32_t max_vertices, double* vertices, double* L, int32_t* flags,
+                    int32_t nthreads) {
+  if (!g || !valid_camera(cam) || !valid_medium(med) || n < 0 || cache_depth < 0 || max_vertices < 0 ||
+      max_vertices > 64 || (max_vertices > 0 && !vertices) || (cache_depth > 0 && !query))
+    return EINVAL_;
+  TetCells cells = {g, (double)med->sigma_scale * g->D.cube};
+  CamRay cr = camera_rays(cam, g->D);
+  auto loc = [&](V3 p) { return locate(g, p); };
+  int nt = set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+  for (int64_t i = 0; i < n; ++i) {
+    CacheIO io;
+    io.depth = cache_depth;
+    io.query = cache_depth > 0 ? query + 8 * i : nullptr;
+    io.vcap = max_vertices;
+    io.vtx = max_vertices > 0 ? vertices + 8 * max_vertices * i : nullptr;
+    PathOut o = trace(cells, g->D, loc, cr, med, seed, px[i], py[i], sample[i], nullptr, 0, &io);
+    if (L) L[i] = o.L;
+    if (flags) flags[i] = o.flags;
   }
   return OK;
 }

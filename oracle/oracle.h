@@ -59,6 +59,20 @@ int orc_render_paths(const orc_grid* g, const orc_camera* cam, const orc_medium*
                      int64_t n, const int32_t* px, const int32_t* py, const int32_t* sample,
                      double* L, int32_t* flags, int32_t* collisions, int64_t* steps,
                      int32_t* seq, int32_t seq_cap, int32_t* seq_len, int32_t nthreads);
+/* The learned radiance cache's two uses of the tracer (8 doubles per record):
+ *  cache_depth > 0: the path ends into the cache at its cache_depth-th collision,
+ *    after that collision's next-event estimate; query[i] = x (3, grid space over
+ *    the domain extent), beta (throughput after the albedo there; 0 when the path
+ *    ended before), d (3, arrival direction), L (estimate so far).
+ *  max_vertices > 0: training samples from the path's first max_vertices
+ *    collisions (the path itself runs to its end when cache_depth = 0):
+ *    vertices[i][j] = x (3), target = (L_final - L after the vertex's NEE) / beta_j,
+ *    d (3), valid (1, or 0 with all zeros past the path's last vertex).
+ *  L[i], flags[i]: the path's own estimate and flags (NULL allowed). */
+int orc_cache_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* med, uint64_t seed,
+                    int64_t n, const int32_t* px, const int32_t* py, const int32_t* sample,
+                    int32_t cache_depth, double* query, int32_t max_vertices, double* vertices,
+                    double* L, int32_t* flags, int32_t nthreads);
 int orc_render(const orc_grid* g, const orc_camera* cam, const orc_medium* med, int32_t spp,
                uint64_t seed, int32_t sample_offset, double* sum, double* sumsq, int64_t* steps,
                int32_t nthreads);

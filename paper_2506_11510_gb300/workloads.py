@@ -339,3 +339,35 @@ def random_path_ids(s: Scene, n: int, seed: int):
     py = torch.randint(0, s.camera.height, (n,), generator=g, dtype=torch.int32)
     sm = torch.randint(0, s.spp, (n,), generator=g, dtype=torch.int32)
     return px, py, sm
+
+
+def mlp_init_params(seed: int, num_params: int = 16641, b4: float = 0.0):
+    """Seeded initial parameters of the radiance cache's MLP (flat fp32 vector in
+    the layout W1[64][128], b1[64], W2[64][64], b2, W3[64][64], b3, w4[64], b4):
+    weights uniform in +-sqrt(6 / fan_in) (He et al. 2015), biases zero."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for fan_out, fan_in in ((64, 128), (64, 64), (64, 64)):
+        lim = math.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    parts.append(rng.uniform(-math.sqrt(6.0 / 64), math.sqrt(6.0 / 64), 64) * 0.1)
+    parts.append(np.array([b4]))
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == num_params
+    return p
+
+
+def mlp_random_records(n: int, seed: int):
+    """Seeded cache records [n][8]: x in [0,1]^3 at 0..2, a unit direction at 4..6,
+    a target / weight in 3 and a valid flag in 7 (1 for 7 of every 8 rows)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = np.zeros((n, 8), np.float32)
+    r[:, 0:3] = rng.uniform(0, 1, (n, 3))
+    d = rng.normal(size=(n, 3))
+    r[:, 4:7] = d / np.linalg.norm(d, axis=1, keepdims=True)
+    r[:, 3] = rng.uniform(0, 2, n)
+    r[:, 7] = (np.arange(n) % 8 != 7).astype(np.float32)
+    return r
