@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-dda", action="store_true", help="skip the regular-grid comparator frame")
     p.add_argument("--cpu-sample-px", type=int, default=0, help="side of the oracle's pixel window (0: auto)")
+    p.add_argument("--no-cache", action="store_true", help="skip the radiance-cache time-to-equal-RMSE leg")
+    p.add_argument("--cache-train-rounds", default="8,32,128", help="training budgets (rounds of 2^16 samples)")
+    p.add_argument("--cache-ref-pixels", type=int, default=4096)
+    p.add_argument("--cache-ref-spp", type=int, default=4096)
     return p.parse_args()
 
 
@@ -236,6 +240,10 @@ def run_ours(args):
                       "voxel_steps_per_path": round((dcount["tet_steps"] + dcount["shadow_steps"]) / paths, 1),
                       "tet_speedup": round(dda_ms / (total_ms / args.steps), 3)}
 
+    cache = None
+    if not args.no_cache and rank == 0:
+        cache = cache_leg(args, s, grid, dev, ms_per_step)
+
     # end to end through the public API: host volume -> device, build, render, image -> host
     e2e = None
     if args.e2e_steps > 0:
@@ -295,10 +303,102 @@ def run_ours(args):
                            "l2": "inputs larger than L2: grid records %.2f GB" % (ntets * 32 / 1e9),
                            "parallelism": "one frame per rank, disjoint sample ranges"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clk, "comparator": comparator}
+                "clocks": clk, "comparator": comparator, "cache": cache}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the learned radiance cache: time to equal RMSE, cached vs plain
+# ---------------------------------------------------------------------------
+def cache_leg(args, s, grid, dev, plain_ms):
+    """RMSE over random pixels against a high-spp plain reference: the plain
+    tracer's at the frame's spp (one frame, plain_ms), and the cached tracer's
+    after online training, at increasing spp; the time to equal RMSE is the
+    training time plus the first cached frame whose RMSE is at most the plain one."""
+    import torch
+    import paper_2506_11510_gb300 as tv
+    from paper_2506_11510_gb300 import cache as RC, workloads as W
+    st = torch.cuda.current_stream()
+    W_, H_ = s.camera.width, s.camera.height
+    npx, ref_spp = args.cache_ref_pixels, args.cache_ref_spp
+    gen = torch.Generator().manual_seed(1234)
+    pix = torch.randperm(W_ * H_, generator=gen)[:npx].to(dev)
+    px, py = (pix % W_).int(), (pix // W_).int()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        out = fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    # reference: ref_spp samples per pixel from a sample range the frames do not use
+    ref = torch.zeros(npx, dtype=torch.float64, device=dev)
+    chunk = max(1, min(ref_spp, (1 << 24) // npx))
+    ref_base = 1 << 20
+    ref_ms = 0.0
+    for s0 in range(0, ref_spp, chunk):
+        k = min(chunk, ref_spp - s0)
+        rx, ry = px.repeat_interleave(k), py.repeat_interleave(k)
+        rs = (ref_base + s0 + torch.arange(k, device=dev, dtype=torch.int32)).repeat(npx)
+        out, ms = timed(lambda: tv.tet_trace_paths(grid, s.camera, s.medium, s.render_seed, rx, ry, rs))
+        ref += out["L"].view(npx, k).double().sum(1)
+        ref_ms += ms
+        del out, rx, ry, rs
+    ref /= ref_spp
+
+    def rmse(img, spp):
+        m = img[py.long(), px.long()].double() / spp
+        return float(torch.sqrt(torch.mean((m - ref) ** 2)))
+
+    plain, _ = tv.tet_render(grid, s.camera, s.medium, s.spp, s.render_seed, 0)
+    target = rmse(plain, s.spp)
+    rel = float(torch.sqrt(torch.mean(ref ** 2)))
+    res = {"reference": "%d spp at %d random pixels (plain tracer, samples from %d)" % (ref_spp, npx, ref_base),
+           "reference_ms": round(ref_ms, 1), "rms_radiance": round(rel, 6),
+           "plain": {"spp": s.spp, "ms": round(plain_ms, 2), "rmse": round(target, 6)}, "variants": []}
+    best = None
+    for rounds in [int(r) for r in str(args.cache_train_rounds).split(",") if r]:
+        for depth in (1, 2):
+            rc = RC.RadianceCache(W.mlp_init_params(1, b4=0.1), device=dev, lr=3e-3)
+            _, train_ms = timed(lambda: rc.train(grid, s.camera, s.medium, s.render_seed, rounds=rounds))
+            curve, reached = [], None
+            for spp in (1, 2, 4, 8, 16, 32):
+                (img, _), ms = timed(lambda: rc.render(grid, s.camera, s.medium, spp, s.render_seed, depth))
+                e = rmse(img, spp)
+                curve.append({"spp": spp, "ms": round(ms, 2), "rmse": round(e, 6)})
+                if reached is None and e <= target:
+                    reached = train_ms + ms
+            v = {"cache_depth": depth, "train_rounds": rounds, "train_samples_per_round": (1 << 14) * 4,
+                 "adam_steps": rc.step, "train_ms": round(train_ms, 2),
+                 "final_train_loss": round(float(rc.loss[2]), 6), "curve": curve,
+                 "time_to_equal_rmse_ms": None if reached is None else round(reached, 2),
+                 "speedup_vs_plain": None if reached is None else round(plain_ms / reached, 3)}
+            res["variants"].append(v)
+            if reached is not None and (best is None or reached < best):
+                best = reached
+    # where training time goes: tracing the training paths, and the grad + Adam steps
+    rc = RC.RadianceCache(W.mlp_init_params(1, b4=0.1), device=dev, lr=3e-3)
+    n_tr = 32 << 14
+    tx, ty, ts = RC.random_paths(77, n_tr, W_, H_, 1 << 24)
+    buf, trace_ms = timed(lambda: RC.cache_samples(grid, s.camera, s.medium, s.render_seed, tx, ty, ts, 4))
+
+    def steps():
+        per = buf.shape[0] // 128
+        for i in range(128):
+            RC.mlp_grad(rc.params, buf[i * per:(i + 1) * per], rc.grad, rc.loss)
+            rc.step += 1
+            RC.adam(rc.params, rc.m, rc.v, rc.grad, rc.loss, rc.step, rc.lr)
+    _, steps_ms = timed(steps)
+    res["train_phases"] = {"trace_paths": n_tr, "trace_ms": round(trace_ms, 2), "steps": 128,
+                           "samples_per_step": buf.shape[0] // 128, "steps_ms": round(steps_ms, 2)}
+    res["time_to_equal_rmse_ms"] = None if best is None else round(best, 2)
+    res["speedup_vs_plain"] = None if best is None else round(plain_ms / best, 3)
+    res["timeouts"] = RC.timeouts()
+    return res
 
 
 # ---------------------------------------------------------------------------

@@ -217,6 +217,114 @@ int tet_optical_depth(const tg_grid* g, int64_t n, const float* origin, const fl
 int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp, uint64_t seed,
                        int32_t sample_offset, float* accum_sum, float* accum_sumsq, void* cuda_stream);
 
+/* ==========================================================================
+ * Learned radiance cache.  A small MLP R(x, d) ends paths after one or two
+ * collisions: it stands for the radiance that the rest of a path brings back,
+ * is trained online on the tracer's own path vertices, and the plain tracer
+ * (tet_render) stays the unbiased reference.  Not in the paper; it follows the
+ * neural radiance caching idea (Mueller et al., SIGGRAPH 2021) on this grid.
+ *
+ * Network (fp32 master parameters, one flat device float[RC_NUM_PARAMS]):
+ *   e(x, d): 128 features -- x (3), d (3), sin and cos of 2^l pi x_a for l < 12,
+ *            sin and cos of 2^l pi d_a for l < 4, zeros; in that order, each
+ *            sin directly before its cos, axis-major
+ *   h1 = relu(W1 e + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3), R = w4 . h3 + b4
+ *   layout: W1[64][128], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], w4[64], b4
+ * The three matrix products run on the tensor cores with BF16 operands (e, h1,
+ * h2 and the weights rounded to nearest even) and FP32 accumulation; biases,
+ * h3, the output layer and all bias gradients stay FP32.
+ *
+ * Records (device float[n][8], 32 bytes each):
+ *   query / cached path: x (3), beta, d (3), L
+ *   training sample:      x (3), target, d (3), valid
+ * x is the grid-space position divided by the domain extent (in [0,1]^3), d the
+ * unit direction the path arrived with, beta the path throughput after the
+ * albedo at x, L the estimate gathered before the cache takes over.
+ * ========================================================================== */
+#define RC_NUM_PARAMS 16641
+
+/*
+ * tg_random_paths - n training paths: pixel i uniform over the W x H image,
+ * drawn as floor(u * W * H) from word 0 of Philox4x32-10 with key (seed lo,
+ * seed hi) and counter (i lo, i hi, 0x52434143, 0); sample[i] = sample_base + i.
+ * px, py, sample: device int32[n].  Asynchronous.  TG_EINVAL on bad sizes.
+ */
+int tg_random_paths(uint64_t seed, int64_t n, int32_t width, int32_t height, int32_t sample_base, int32_t* px,
+                    int32_t* py, int32_t* sample, void* cuda_stream);
+
+/*
+ * tet_cache_samples - training samples from full paths: the n listed paths run
+ * to their end as in tet_trace_paths; the first max_vertices (<= 64) collisions
+ * of path i, after their next-event estimate, become samples
+ * samples[i][j] = (x, target, d, valid) with target = (L_final - L_j) / beta_j,
+ * the rest of the path's estimate per unit throughput (L_j: the estimate after
+ * vertex j's NEE); slots past the path's last collision are all zero.
+ * samples: device float[n][max_vertices][8]; L: device float[n] or NULL.
+ * Asynchronous.  Shares the grid's scratch counter: serialise with other calls.
+ */
+int tet_cache_samples(const tg_grid* g, const tg_camera* cam, const tg_medium* med, uint64_t seed, int64_t n,
+                      const int32_t* px, const int32_t* py, const int32_t* sample, int32_t max_vertices,
+                      float* samples, float* L, void* cuda_stream);
+
+/*
+ * tet_cache_queries - the cached estimator's paths for n listed paths: a path
+ * ends into the cache at its cache_depth-th collision (>= 1), after that
+ * collision's NEE, unless it escaped or was truncated before.
+ * rec[i] = (x, beta, d, L): beta = 0 (and x = d = 0) for a path that did not
+ * reach the cache; its estimate is then L.  rec: device float[n][8].
+ * The cached estimate of path i is L + beta * max(R(x, d), 0).  Asynchronous.
+ */
+int tet_cache_queries(const tg_grid* g, const tg_camera* cam, const tg_medium* med, uint64_t seed, int64_t n,
+                      const int32_t* px, const int32_t* py, const int32_t* sample, int32_t cache_depth,
+                      float* rec, void* cuda_stream);
+
+/*
+ * rc_mlp_infer - R(x, d) for n records (queries or samples; only x and d are
+ * read): y: device float[n].  params: device float[RC_NUM_PARAMS].
+ * One fused kernel (encoding, three tensor-core layers, output) over tiles of
+ * 128 records.  Asynchronous.  If a tensor-core completion wait ever runs out
+ * (it should not), the affected rows are NaN and rc_timeouts() counts it.
+ */
+int rc_mlp_infer(const float* params, const float* rec, int64_t n, float* y, void* cuda_stream);
+
+/*
+ * rc_mlp_grad - the L2 loss sum_i valid_i (R(x_i, d_i) - target_i)^2 over n
+ * training samples and its gradient: grad (device float[RC_NUM_PARAMS]) += the
+ * gradient of that sum (not divided by the count); loss (device float[3]):
+ * loss[0] += the sum, loss[1] += sum_i valid_i.  One fused forward + backward
+ * kernel; weight gradients accumulate in tensor memory across a block's tiles.
+ * Asynchronous.
+ */
+int rc_mlp_grad(const float* params, const float* samples, int64_t n, float* grad, float* loss, void* cuda_stream);
+
+/*
+ * rc_adam - one Adam step (Kingma & Ba 2015) on the mean gradient
+ * grad / max(loss[1], 1), step counted from 1; m and v (device
+ * float[RC_NUM_PARAMS]) are the moment estimates.  Afterwards grad, loss[0] and
+ * loss[1] are zero and loss[2] = loss[0] / max(loss[1], 1) of the step.
+ * Asynchronous.  TG_EINVAL for step < 1 or a bad hyper-parameter.
+ */
+int rc_adam(float* params, float* m, float* v, float* grad, float* loss, int32_t step, float lr, float beta1,
+            float beta2, float eps, void* cuda_stream);
+
+/*
+ * tet_render_cached - a frame of the cached estimator: as tet_render (same
+ * pixels, samples, random numbers and accumulation), but every path that
+ * reaches its cache_depth-th collision ends there into the cache:
+ * L + beta * max(R(x, d), 0) per path.  Three launches: the tracer writing one
+ * record per path into the grid's scratch pool (32 bytes x W x H x spp, grown
+ * on first use and kept with the grid), the fused MLP completing the records,
+ * and a per-pixel sum in sample order.  Asynchronous; serialise calls on the
+ * same grid.
+ */
+int tet_render_cached(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp, uint64_t seed,
+                      int32_t sample_offset, int32_t cache_depth, const float* params, float* accum_sum,
+                      float* accum_sumsq, tg_stats* stats, void* cuda_stream);
+
+/* rc_timeouts - number of tensor-core completion waits that ran out since the
+ * library was loaded (0 in a healthy run).  Synchronises the device. */
+int rc_timeouts(int64_t* count);
+
 const char* tg_error_string(int status);
 
 #ifdef __cplusplus

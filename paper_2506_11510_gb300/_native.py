@@ -53,8 +53,21 @@ SIGNATURES = {
     "tet_optical_depth": (C.c_int, [_VP, _I64, _VP, _VP, _F, _VP, _VP, _VP, _I32, _VP, _VP]),
     "tet_render_noalloc": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _I32, _U64, _I32, _VP, _VP,
                                      _VP]),
+    "tg_random_paths": (C.c_int, [_U64, _I64, _I32, _I32, _I32, _VP, _VP, _VP, _VP]),
+    "tet_cache_samples": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _U64, _I64, _VP, _VP, _VP, _I32,
+                                    _VP, _VP, _VP]),
+    "tet_cache_queries": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _U64, _I64, _VP, _VP, _VP, _I32,
+                                    _VP, _VP]),
+    "rc_mlp_infer": (C.c_int, [_VP, _VP, _I64, _VP, _VP]),
+    "rc_mlp_grad": (C.c_int, [_VP, _VP, _I64, _VP, _VP, _VP]),
+    "rc_adam": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _I32, _F, _F, _F, _F, _VP]),
+    "tet_render_cached": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _I32, _U64, _I32, _I32, _VP, _VP,
+                                    _VP, _VP, _VP]),
+    "rc_timeouts": (C.c_int, [C.POINTER(_I64)]),
     "tg_error_string": (C.c_char_p, [C.c_int]),
 }
+
+RC_NUM_PARAMS = 16641
 
 _lib = None
 

@@ -80,6 +80,8 @@ struct GridImpl {
   unsigned long long* scratch = nullptr; // work counter of the persistent renderer
   int32_t* locator = nullptr;            // cell of each locator-grid cell centre (loc_R per cube edge)
   int loc_R = 0;
+  float* pool = nullptr;                 // scratch pool of the cached renderer (grown on demand)
+  size_t pool_floats = 0;
   ~GridImpl();
 };
 

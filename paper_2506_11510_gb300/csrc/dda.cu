@@ -43,6 +43,7 @@ static EstParams dda_est(const tg_camera& cam, const tg_medium& med, uint64_t se
   ep.seed = seed;
   ep.regen_min = TV_REGEN_MIN;
   ep.ev_min = TV_EV_MIN;
+  for (int a = 0; a < 3; ++a) ep.ext[a] = 1.0f;
   return ep;
 }
 
@@ -74,7 +75,7 @@ int grid_render(const float* density, const tg_volume_desc* vol, const tg_camera
     ep.sumsq = accum_sumsq;
     ep.stats = stats;
     TV_CUDA(cudaMemsetAsync(ep.counter, 0, sizeof(unsigned long long), st));
-    launch_estimate<VoxelWalker, false>(p, ep, st);
+    launch_estimate<VoxelWalker, MODE_RENDER>(p, ep, st);
   } catch (const Error& e) {
     return e.code;
   }
@@ -101,7 +102,7 @@ int grid_trace_paths(const float* density, const tg_volume_desc* vol, const tg_c
     ep.px = px; ep.py = py; ep.ps = sample;
     ep.outL = L; ep.outFlags = flags; ep.outColl = collisions; ep.outSteps = steps;
     TV_CUDA(cudaMemsetAsync(ep.counter, 0, sizeof(unsigned long long), st));
-    launch_estimate<VoxelWalker, true>(p, ep, st);
+    launch_estimate<VoxelWalker, MODE_TRACE>(p, ep, st);
   } catch (const Error& e) {
     return e.code;
   }

@@ -65,6 +65,10 @@ constexpr int SEG_STEP_LIMIT = 1 << 20;      // cells per segment before a walk 
 // E * beta * p * e^-40 < 1e-16 and is stopped early (not in trace mode).
 constexpr float SHADOW_TAU_CUTOFF = 40.0f;
 
+// What the kernel does with a finished path: add it to the image (render),
+// write per-path outputs for a list of paths (trace), or write a per-path
+// record for the radiance cache to complete (cached render).
+enum : int { MODE_RENDER = 0, MODE_TRACE = 1, MODE_CACHED = 2 };
 enum : int { S_IDLE = 0, S_WALK = 1, S_EVENT = 2, S_DONE = 3 };
 enum : int { M_FREE = 0, M_SHADOW = 1 };
 enum : int { EV_LIMIT = 1, EV_BOUNDARY = 2 };
@@ -95,7 +99,28 @@ struct EstParams {
   int32_t* seq;
   int32_t seq_cap;
   int32_t* seq_len;
+  // learned radiance cache (trace and cached modes)
+  int cache_depth;                          // > 0: a path ends into the cache at this collision
+  float* cache_rec;                         // [path][8]: x (3), beta, d (3), L so far
+  int vtx_cap;                              // trace mode: training samples from the first vtx_cap collisions
+  float* vtx;                               // [path][vtx_cap][8]: x (3), target, d (3), valid
+  float ext[3];                             // domain extent in grid units (positions are stored over it)
 };
+
+// Pixel of the pix-th pixel in render order: TV_TILE x TV_TILE tiles, row-major
+// tiles, row-major inside a tile (when the tiles divide the image).
+__device__ __forceinline__ void render_pixel(long long pix, int W, int H, int* px, int* py) {
+  if (TV_TILE > 1 && W % TV_TILE == 0 && H % TV_TILE == 0) {
+    const long long tile = pix / (TV_TILE * TV_TILE);
+    const int in = (int)(pix - tile * (TV_TILE * TV_TILE));
+    const int tpr = W / TV_TILE;
+    *px = (int)(tile % tpr) * TV_TILE + in % TV_TILE;
+    *py = (int)(tile / tpr) * TV_TILE + in / TV_TILE;
+  } else {
+    *px = (int)(pix % W);
+    *py = (int)(pix / W);
+  }
+}
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 #pragma unroll
@@ -122,9 +147,10 @@ __device__ __forceinline__ bool box_intersect(const int C[3], float3 o, float3 d
   return tn < tf;
 }
 
-template <class Walker, bool TRACE>
+template <class Walker, int MODE>
 __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const typename Walker::Params wp,
                                                                           const EstParams ep) {
+  constexpr bool TRACE = MODE == MODE_TRACE;
   extern __shared__ double smem_d[];
   __shared__ float sun_inv[Walker::NDIR];
   Walker W(wp, smem_d);
@@ -150,6 +176,8 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
   float beta = 1.f;
   ff L = ff_make(0.f);
   int bounce = 0, seg_steps = 0, flags = 0, ncoll = 0, saved = 0, seqn = 0;
+  int nv = 0;                                          // cache training vertices recorded
+  bool queried = false;                                // the path ended into the cache
   long long psteps = 0;
   uint32_t c_paths = 0, c_steps = 0, c_shadow = 0, c_coll = 0, c_esc = 0, c_trunc = 0, c_lim = 0, c_miss = 0;
 
@@ -161,16 +189,39 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
   };
   auto finish = [&]() {
     ++c_paths;
+    const float Lf = ff_float(L);
     if (TRACE) {
-      if (ep.outL) ep.outL[pid] = ff_float(L);
+      if (ep.outL) ep.outL[pid] = Lf;
       if (ep.outFlags) ep.outFlags[pid] = flags;
       if (ep.outColl) ep.outColl[pid] = ncoll;
       if (ep.outSteps) ep.outSteps[pid] = psteps;
       if (ep.seq_len) ep.seq_len[pid] = seqn < ep.seq_cap ? seqn : ep.seq_cap;
-    } else {
-      const float Lf = ff_float(L);
+      if (ep.vtx) {
+        // training targets: the rest of this path's estimate after each recorded vertex
+        float4* v = reinterpret_cast<float4*>(ep.vtx) + 2 * (long long)ep.vtx_cap * pid;
+        for (int j = 0; j < ep.vtx_cap; ++j) {
+          float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+          if (j < nv) {
+            a = v[2 * j];
+            b = v[2 * j + 1];
+            const float bj = a.w;
+            a.w = bj > 0.f ? (Lf - b.w) / bj : 0.f;
+            b.w = bj > 0.f ? 1.f : 0.f;
+            if (bj <= 0.f) a = b = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          v[2 * j] = a;
+          v[2 * j + 1] = b;
+        }
+      }
+    }
+    if (MODE == MODE_RENDER) {
       atomicAdd(ep.sum + pixel, Lf);
       if (ep.sumsq) atomicAdd(ep.sumsq + pixel, Lf * Lf);
+    }
+    if (MODE != MODE_RENDER && ep.cache_rec && !queried) {
+      float4* r = reinterpret_cast<float4*>(ep.cache_rec) + 2 * pid;
+      r[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      r[1] = make_float4(0.f, 0.f, 0.f, Lf);
     }
     state = S_IDLE;
   };
@@ -210,20 +261,12 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
             // cells the warps in flight touch close together
             const long long pix = pid / ep.spp;
             s = ep.sample_offset + (int)(pid - pix * ep.spp);
-            if (TV_TILE > 1 && ep.cam.W % TV_TILE == 0 && ep.cam.H % TV_TILE == 0) {
-              const long long tile = pix / (TV_TILE * TV_TILE);
-              const int in = (int)(pix - tile * (TV_TILE * TV_TILE));
-              const int tpr = ep.cam.W / TV_TILE;
-              px = (int)(tile % tpr) * TV_TILE + in % TV_TILE;
-              py = (int)(tile / tpr) * TV_TILE + in / TV_TILE;
-            } else {
-              px = (int)(pix % ep.cam.W);
-              py = (int)(pix / ep.cam.W);
-            }
+            render_pixel(pix, ep.cam.W, ep.cam.H, &px, &py);
           }
           pixel = (uint32_t)(py * ep.cam.W + px);
           sample = (uint32_t)s;
           flags = 0; ncoll = 0; psteps = 0; seqn = 0; L = ff_make(0.f); beta = 1.f; bounce = 0;
+          nv = 0; queried = false;
           const double u0 = rng_u(ep.seed, pixel, sample, 0), u1 = rng_u(ep.seed, pixel, sample, 1);
           const CamF& c = ep.cam;
           const double sx = (2.0 * (((double)px + u0) / (double)c.W) - 1.0) * c.tanF * c.aspect;
@@ -286,8 +329,23 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
         const float tr = ev == EV_BOUNDARY ? expf(-ff_float(acc)) : 0.0f;
         const float cs = d.x.hi * M.sun_w[0] + d.y.hi * M.sun_w[1] + d.z.hi * M.sun_w[2];
         L = ff_add(L, ff_make(beta * hg_eval(M.g, cs) * M.E * tr));
+        const float4 xq = make_float4(ff_float(o.x) / ep.ext[0], ff_float(o.y) / ep.ext[1],
+                                      ff_float(o.z) / ep.ext[2], beta);
+        if (TRACE && ep.vtx && nv < ep.vtx_cap) {
+          float4* v = reinterpret_cast<float4*>(ep.vtx) + 2 * ((long long)ep.vtx_cap * pid + nv);
+          v[0] = xq;
+          v[1] = make_float4(d.x.hi, d.y.hi, d.z.hi, ff_float(L));
+          ++nv;
+        }
         if (bounce + 1 >= M.max_bounces) {
           flags |= 2; ++c_trunc;
+          finish();
+        } else if (MODE != MODE_RENDER && ep.cache_depth > 0 && bounce + 1 == ep.cache_depth) {
+          // the path ends into the radiance cache, which stands for the rest of it
+          float4* r = reinterpret_cast<float4*>(ep.cache_rec) + 2 * pid;
+          r[0] = xq;
+          r[1] = make_float4(d.x.hi, d.y.hi, d.z.hi, ff_float(L));
+          queried = true;
           finish();
         } else {
           // SamplePhaseFunction, then a new free flight from the collision point
@@ -348,18 +406,18 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
 }
 
 // Launch the persistent estimator: as many resident blocks as fit, one wave.
-template <class Walker, bool TRACE>
+template <class Walker, int MODE>
 void launch_estimate(const typename Walker::Params& wp, const EstParams& ep, cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   TV_CUDA(cudaGetDevice(&dev));
   TV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const size_t shm = Walker::smem_bytes();
-  TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<Walker, TRACE>, EST_BLOCK, shm));
+  TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<Walker, MODE>, EST_BLOCK, shm));
   if (per_sm < 1) per_sm = 1;
   long long blocks = (long long)sms * per_sm;
   const long long need = (ep.total + EST_BLOCK - 1) / EST_BLOCK;
   if (blocks > need) blocks = need < 1 ? 1 : need;
-  k_estimate<Walker, TRACE><<<(unsigned)blocks, EST_BLOCK, shm, st>>>(wp, ep);
+  k_estimate<Walker, MODE><<<(unsigned)blocks, EST_BLOCK, shm, st>>>(wp, ep);
   TV_LAUNCH();
 }
 

@@ -97,23 +97,13 @@ extern "C" int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const 
     ep.seed = seed;
     ep.regen_min = TV_REGEN_MIN;
     ep.ev_min = TV_EV_MIN;
+    for (int a = 0; a < 3; ++a) ep.ext[a] = (float)G.C[a];
     ep.spp = 1;
     ep.total = n;
     ep.counter = counter;
     ep.px = px; ep.py = py; ep.ps = ps;
     ep.outL = L;
-    TetParams p;
-    p.rec = G.rec; p.codes = G.codes; p.n = G.n; p.K = G.K; p.depth = G.max_depth;
-    for (int a = 0; a < 3; ++a) p.C[a] = G.C[a];
-    p.scaleK = std::ldexp(1.0f, G.K);
-    p.invK = std::ldexp(1.0f, -G.K);
-    p.locator = G.locator;
-    p.R = G.loc_R;
-    switch (G.fmt) {
-      case TG_DENSITY_BF16: launch_estimate<TetWalker<TG_DENSITY_BF16>, true>(p, ep, st); break;
-      case TG_DENSITY_FP16: launch_estimate<TetWalker<TG_DENSITY_FP16>, true>(p, ep, st); break;
-      default: launch_estimate<TetWalker<TG_DENSITY_FP32>, true>(p, ep, st); break;
-    }
+    run_tet<MODE_TRACE>(G, ep, st);
     k_noalloc_sum<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(L, npix, spp, accum_sum, accum_sumsq);
     TV_LAUNCH();
   } catch (const Error& e) {

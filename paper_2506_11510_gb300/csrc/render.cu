@@ -10,7 +10,7 @@ GridImpl::~GridImpl() {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator};
+  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator, pool};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (prev >= 0) cudaSetDevice(prev);
@@ -72,7 +72,7 @@ bool camera_ok(const tg_camera* c) {
 
 bool medium_ok(const tg_medium* m) { return m && m->max_bounces >= 1 && m->g > -1.f && m->g < 1.f; }
 
-static TetParams tet_params(const GridImpl& g) {
+TetParams tet_params(const GridImpl& g) {
   TetParams p;
   p.rec = g.rec;
   p.codes = g.codes;
@@ -113,17 +113,7 @@ void build_locator(GridImpl& G, cudaStream_t st) {
   G.loc_R = R;
 }
 
-template <bool TRACE>
-static void run_tet(const GridImpl& g, const EstParams& ep, cudaStream_t st) {
-  const TetParams p = tet_params(g);
-  switch (g.fmt) {
-    case TG_DENSITY_BF16: launch_estimate<TetWalker<TG_DENSITY_BF16>, TRACE>(p, ep, st); break;
-    case TG_DENSITY_FP16: launch_estimate<TetWalker<TG_DENSITY_FP16>, TRACE>(p, ep, st); break;
-    default: launch_estimate<TetWalker<TG_DENSITY_FP32>, TRACE>(p, ep, st); break;
-  }
-}
-
-static EstParams est_params(const GridImpl& g, const tg_camera& cam, const tg_medium& med, uint64_t seed) {
+EstParams est_params(const GridImpl& g, const tg_camera& cam, const tg_medium& med, uint64_t seed) {
   EstParams ep;
   std::memset(&ep, 0, sizeof ep);
   ep.cam = camera_setup(cam, g.box_min, g.cube);
@@ -131,6 +121,7 @@ static EstParams est_params(const GridImpl& g, const tg_camera& cam, const tg_me
   ep.seed = seed;
   ep.regen_min = TV_REGEN_MIN;
   ep.ev_min = TV_EV_MIN;
+  for (int a = 0; a < 3; ++a) ep.ext[a] = (float)g.C[a];
   return ep;
 }
 
@@ -239,7 +230,7 @@ int tet_render(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int
   ep.sumsq = accum_sumsq;
   ep.stats = stats;
   TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
-  run_tet<false>(G, ep, st);
+  run_tet<MODE_RENDER>(G, ep, st);
   return TG_OK;
   TV_API_END
 }
@@ -263,7 +254,7 @@ int tet_trace_paths(const tg_grid* g, const tg_camera* cam, const tg_medium* med
   ep.outL = L; ep.outFlags = flags; ep.outColl = collisions; ep.outSteps = steps;
   ep.seq = seq; ep.seq_cap = seq ? seq_cap : 0; ep.seq_len = seq_len;
   TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
-  run_tet<true>(G, ep, st);
+  run_tet<MODE_TRACE>(G, ep, st);
   return TG_OK;
   TV_API_END
 }

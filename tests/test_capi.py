@@ -54,3 +54,33 @@ def test_argument_checks_need_no_gpu():
     assert L.leb_build(C.c_void_p(16), C.byref(desc), None, 0.0, -1.0, 4, 3, None, C.byref(out)) == N.TG_EINVAL
     assert L.tet_render(None, None, None, 1, 0, 0, None, None, None, None) == N.TG_EINVAL
     assert L.tg_grid_info(None, None, None, None, None, None) == N.TG_EINVAL
+
+
+def test_radiance_cache_argument_checks_need_no_gpu():
+    import ctypes as C
+    from paper_2506_11510_gb300 import _native as N
+    L = N.lib()
+    cam, med = N.TgCamera(), N.TgMedium()
+    cam.width = cam.height = 8
+    cam.fov_y_deg = 40.0
+    med.max_bounces = 4
+    fake = C.c_void_p(256)
+    assert L.rc_adam(fake, fake, fake, fake, fake, 0, 1e-3, 0.9, 0.99, 1e-8, None) == N.TG_EINVAL    # step < 1
+    assert L.rc_adam(fake, fake, fake, fake, fake, 1, 0.0, 0.9, 0.99, 1e-8, None) == N.TG_EINVAL     # lr
+    assert L.rc_adam(fake, fake, fake, fake, fake, 1, 1e-3, 1.0, 0.99, 1e-8, None) == N.TG_EINVAL    # beta1
+    assert L.rc_mlp_infer(None, fake, 4, fake, None) == N.TG_EINVAL
+    assert L.rc_mlp_infer(fake, None, 4, fake, None) == N.TG_EINVAL
+    assert L.rc_mlp_grad(fake, fake, -1, fake, fake, None) == N.TG_EINVAL
+    assert L.rc_mlp_grad(fake, fake, 0, None, fake, None) == N.TG_EINVAL
+    assert L.tet_render_cached(None, C.byref(cam), C.byref(med), 1, 0, 0, 1, fake, fake, None, None,
+                               None) == N.TG_EINVAL
+    assert L.tet_render_cached(fake, C.byref(cam), C.byref(med), 1, 0, 0, 0, fake, fake, None, None,
+                               None) == N.TG_EINVAL                                               # depth 0
+    assert L.tet_cache_queries(fake, C.byref(cam), C.byref(med), 0, 4, fake, fake, fake, 0, fake,
+                               None) == N.TG_EINVAL
+    assert L.tet_cache_samples(fake, C.byref(cam), C.byref(med), 0, 4, fake, fake, fake, 65, fake, None,
+                               None) == N.TG_EINVAL                                               # > 64 vertices
+    assert L.tg_random_paths(0, 4, 0, 8, 0, fake, fake, fake, None) == N.TG_EINVAL
+    assert L.tg_random_paths(0, 4, 8, 8, (1 << 31) - 2, fake, fake, fake, None) == N.TG_EINVAL
+    assert L.rc_mlp_grad(fake, fake, 0, fake, fake, None) == N.TG_OK                              # nothing to do
+    assert N.RC_NUM_PARAMS == 64 * 128 + 64 + 2 * (64 * 64 + 64) + 64 + 1
