@@ -29,7 +29,7 @@ namespace {
 
 constexpr unsigned long long EMPTY = ~0ull;
 constexpr int TPB = 256;
-constexpr int CHUNK = 256;          // voxels per warp work item of the statistics pass
+constexpr int ROWS = 32;            // voxel-box rows per warp work item of the statistics pass (one per lane)
 
 struct Geo {
   int nx, ny, nz, n, m, K, max_depth;
@@ -253,7 +253,8 @@ __device__ __forceinline__ void tet_box(const int x[4][3], const Geo& g, int lo[
   }
 }
 
-// A3 statistics, pass 1: chunk counts of the new leaves; reset their statistics
+// A3 statistics, pass 1: work items of the new leaves (ROWS rows of the leaf's
+// voxel box each); reset their statistics
 __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo g, unsigned long long* chunks) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
@@ -261,18 +262,26 @@ __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo
   int x[4][3], lo[3], hi[3];
   load_tet(L.v, i, x);
   tet_box(x, g, lo, hi);
-  long long w = 1;
-  for (int a = 0; a < 3; ++a) w *= (hi[a] >= lo[a]) ? (long long)(hi[a] - lo[a] + 1) : 0;
-  chunks[j] = (unsigned long long)((w + CHUNK - 1) / CHUNK);
+  long long rows = 0;
+  if (hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2])
+    rows = (long long)(hi[1] - lo[1] + 1) * (long long)(hi[2] - lo[2] + 1);
+  chunks[j] = (unsigned long long)((rows + ROWS - 1) / ROWS);
   L.cnt[i] = 0; L.sum[i] = 0; L.mn[i] = 0xFFFFFFFFu; L.mx[i] = 0;
 }
 
-// A3 statistics, pass 2: one warp per chunk of a leaf's voxel box
+// A3 statistics, pass 2: one warp per ROWS rows (along x) of a leaf's voxel box,
+// one row per lane.  The voxel centres P = (2i+1, 2j+1, 2k+1) h of a row that lie
+// in the closed tet form an interval of i, found exactly from the four faces
+// n . P <= rhs (n in {0, +-1}^3, h a power of two): with F = floor(B / h),
+// B = rhs - n_y (2j+1) h - n_z (2k+1) h, a face with n_x = 1 gives
+// i <= floor((F - 1) / 2), n_x = -1 gives i >= ceil((-F - 1) / 2), and n_x = 0
+// keeps the row iff B >= 0.  Only the voxels inside are read.
 __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long* list, long long m,
                                                     const unsigned long long* chunk_off, unsigned long long total,
                                                     const uint32_t* __restrict__ q, Geo g) {
   const unsigned lane = threadIdx.x & 31u;
   const long long warps = (long long)gridDim.x * (TPB / 32);
+  const int hs = g.K - g.m - 1;                     // h = 2^hs
   for (long long c = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5); c < (long long)total; c += warps) {
     // leaf j: last chunk_off[j] <= c
     long long lo_j = 0, hi_j = m;
@@ -289,23 +298,26 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long*
     long long rhs[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
-    const long long wx = hi[0] - lo[0] + 1, wy = hi[1] - lo[1] + 1, wz = hi[2] - lo[2] + 1;
-    const long long W = wx * wy * wz;
-    const long long start = ((long long)c - (long long)chunk_off[j]) * CHUNK;
-    const long long end = min(start + CHUNK, W);
+    const long long wy = hi[1] - lo[1] + 1;
+    const long long rows = wy * (hi[2] - lo[2] + 1);
+    const long long r = ((long long)c - (long long)chunk_off[j]) * ROWS + lane;
     uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
     unsigned long long sum = 0;
-    for (long long l = start + lane; l < end; l += 32) {
-      const int ii = lo[0] + (int)(l % wx);
-      const int jj = lo[1] + (int)((l / wx) % wy);
-      const int kk = lo[2] + (int)(l / (wx * wy));
-      const long long P[3] = {(2ll * ii + 1) * g.h, (2ll * jj + 1) * g.h, (2ll * kk + 1) * g.h};
-      bool in = true;
+    if (r < rows) {
+      const int jj = lo[1] + (int)(r % wy), kk = lo[2] + (int)(r / wy);
+      const long long Py = (2ll * jj + 1) << hs, Pz = (2ll * kk + 1) << hs;
+      long long xa = lo[0], xb = hi[0];
 #pragma unroll
-      for (int f = 0; f < 4; ++f)
-        in = in && (nrm[f][0] * P[0] + nrm[f][1] * P[1] + nrm[f][2] * P[2] <= rhs[f]);
-      if (in) {
-        const uint32_t v = __ldg(q + ((size_t)kk * g.ny + jj) * g.nx + ii);
+      for (int f = 0; f < 4; ++f) {
+        const long long B = rhs[f] - nrm[f][1] * Py - nrm[f][2] * Pz;
+        const long long F = B >> hs;                 // floor(B / h)
+        if (nrm[f][0] > 0) xb = min(xb, (F - 1) >> 1);
+        else if (nrm[f][0] < 0) xa = max(xa, -((F + 1) >> 1));
+        else if (B < 0) xb = xa - 1;
+      }
+      const uint32_t* row = q + ((size_t)kk * g.ny + jj) * g.nx;
+      for (long long ii = xa; ii <= xb; ++ii) {
+        const uint32_t v = __ldg(row + ii);
         ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
       }
     }
