@@ -253,6 +253,33 @@ __device__ __forceinline__ void tet_box(const int x[4][3], const Geo& g, int lo[
   }
 }
 
+// A box of at most 32 rows of at most 32 voxels: one thread scans it.
+__device__ __forceinline__ bool small_box(const int lo[3], const int hi[3]) {
+  return (long long)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) <= 32 && hi[0] - lo[0] < 32;
+}
+
+// The voxel centres P = (2i+1, 2j+1, 2k+1) h of row (j, k) that lie in the closed
+// tet form an interval [xa, xb] of i (xb < xa: none), found exactly from the four
+// faces n . P <= rhs (n in {0, +-1}^3, h = 2^hs): with F = floor(B / h),
+// B = rhs - n_y (2j+1) h - n_z (2k+1) h, a face with n_x = 1 gives
+// i <= floor((F - 1) / 2), n_x = -1 gives i >= ceil((-F - 1) / 2), and n_x = 0
+// keeps the row iff B >= 0.
+__device__ __forceinline__ void row_interval(const int nrm[4][3], const long long rhs[4], int hs, int jj, int kk,
+                                             int x0, int x1, int* xa, int* xb) {
+  const long long Py = (2ll * jj + 1) << hs, Pz = (2ll * kk + 1) << hs;
+  long long a = x0, b = x1;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const long long B = rhs[f] - nrm[f][1] * Py - nrm[f][2] * Pz;
+    const long long F = B >> hs;                 // floor(B / h)
+    if (nrm[f][0] > 0) b = min(b, (F - 1) >> 1);
+    else if (nrm[f][0] < 0) a = max(a, -((F + 1) >> 1));
+    else if (B < 0) b = a - 1;
+  }
+  *xa = (int)a;
+  *xb = (int)max(b, a - 1);
+}
+
 // A3 statistics, pass 1: work items of the new leaves (ROWS rows of the leaf's
 // voxel box each); reset their statistics
 __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo g, unsigned long long* chunks) {
@@ -265,17 +292,15 @@ __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo
   long long rows = 0;
   if (hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2])
     rows = (long long)(hi[1] - lo[1] + 1) * (long long)(hi[2] - lo[2] + 1);
-  chunks[j] = (unsigned long long)((rows + ROWS - 1) / ROWS);
+  // small boxes are scanned by one thread in k_stats_finish
+  chunks[j] = small_box(lo, hi) ? 0ull : (unsigned long long)((rows + ROWS - 1) / ROWS);
   L.cnt[i] = 0; L.sum[i] = 0; L.mn[i] = 0xFFFFFFFFu; L.mx[i] = 0;
 }
 
-// A3 statistics, pass 2: one warp per ROWS rows (along x) of a leaf's voxel box,
-// one row per lane.  The voxel centres P = (2i+1, 2j+1, 2k+1) h of a row that lie
-// in the closed tet form an interval of i, found exactly from the four faces
-// n . P <= rhs (n in {0, +-1}^3, h a power of two): with F = floor(B / h),
-// B = rhs - n_y (2j+1) h - n_z (2k+1) h, a face with n_x = 1 gives
-// i <= floor((F - 1) / 2), n_x = -1 gives i >= ceil((-F - 1) / 2), and n_x = 0
-// keeps the row iff B >= 0.  Only the voxels inside are read.
+// A3 statistics, pass 2 (leaves with larger boxes): one warp per ROWS rows
+// (along x) of a leaf's voxel box, one row interval per lane (row_interval), so
+// only the voxels inside are read: by the whole warp along each row in turn when
+// the box is at least 32 voxels wide (coalesced), else by each lane along its row.
 __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long* list, long long m,
                                                     const unsigned long long* chunk_off, unsigned long long total,
                                                     const uint32_t* __restrict__ q, Geo g) {
@@ -303,21 +328,27 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long*
     const long long r = ((long long)c - (long long)chunk_off[j]) * ROWS + lane;
     uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
     unsigned long long sum = 0;
+    int xa = 0, xb = -1;
+    long long rowoff = 0;
     if (r < rows) {
       const int jj = lo[1] + (int)(r % wy), kk = lo[2] + (int)(r / wy);
-      const long long Py = (2ll * jj + 1) << hs, Pz = (2ll * kk + 1) << hs;
-      long long xa = lo[0], xb = hi[0];
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const long long B = rhs[f] - nrm[f][1] * Py - nrm[f][2] * Pz;
-        const long long F = B >> hs;                 // floor(B / h)
-        if (nrm[f][0] > 0) xb = min(xb, (F - 1) >> 1);
-        else if (nrm[f][0] < 0) xa = max(xa, -((F + 1) >> 1));
-        else if (B < 0) xb = xa - 1;
+      row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
+      rowoff = ((long long)kk * g.ny + jj) * g.nx;
+    }
+    if (hi[0] - lo[0] >= 31) {
+      // wide box: the warp reads one row at a time, lanes along x (coalesced)
+      for (int k = 0; k < 32; ++k) {
+        const int a = __shfl_sync(~0u, xa, k), b = __shfl_sync(~0u, xb, k);
+        const long long ro = __shfl_sync(~0u, rowoff, k);
+        for (int ii = a + (int)lane; ii <= b; ii += 32) {
+          const uint32_t v = __ldg(q + ro + ii);
+          ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+        }
       }
-      const uint32_t* row = q + ((size_t)kk * g.ny + jj) * g.nx;
-      for (long long ii = xa; ii <= xb; ++ii) {
-        const uint32_t v = __ldg(row + ii);
+    } else {
+      // narrow box: one row per lane
+      for (int ii = xa; ii <= xb; ++ii) {
+        const uint32_t v = __ldg(q + rowoff + ii);
         ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
       }
     }
@@ -388,6 +419,30 @@ __global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, c
   int x[4][3];
   load_tet(L.v, i, x);
   const Geo& g = C.g;
+  {
+    int lo[3], hi[3];
+    tet_box(x, g, lo, hi);
+    if (hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2] && small_box(lo, hi)) {
+      int nrm[4][3];
+      long long rhs[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
+      const int hs = g.K - g.m - 1;
+      uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
+      unsigned long long sum = 0;
+      for (int kk = lo[2]; kk <= hi[2]; ++kk)
+        for (int jj = lo[1]; jj <= hi[1]; ++jj) {
+          int xa, xb;
+          row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
+          const uint32_t* row = q + ((size_t)kk * g.ny + jj) * g.nx;
+          for (int ii = xa; ii <= xb; ++ii) {
+            const uint32_t v = __ldg(row + ii);
+            ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+          }
+        }
+      L.cnt[i] = cnt; L.sum[i] = sum; L.mn[i] = mn; L.mx[i] = mx;
+    }
+  }
   if (L.cnt[i] == 0) {
     const int dims[3] = {g.nx, g.ny, g.nz};
     int idx[3];
