@@ -44,6 +44,10 @@ class _Medium(C.Structure):
                 ("sun_irradiance", C.c_float), ("env_radiance", C.c_float)]
 
 
+class _Ext(C.Structure):
+    _fields_ = [("flags", C.c_int32), ("emission_scale", C.c_float), ("density", C.c_void_p)]
+
+
 def camera_struct(cam) -> _Camera:
     c = _Camera()
     c.pos[:] = list(cam.pos); c.target[:] = list(cam.target); c.up[:] = list(cam.up)
@@ -71,6 +75,7 @@ def lib():
         _lib.orc_uniform.restype = C.c_double
         _lib.orc_hg_pdf.restype = C.c_double
         _lib.orc_grid_free.restype = None
+        _lib.orc_render_ext_paths.argtypes = None
     return _lib
 
 
@@ -191,6 +196,36 @@ class Grid:
                                      C.c_uint64(seed), C.c_int64(n), _p(px), _p(py), _p(sm), cache_depth, _p(q),
                                      max_vertices, _p(v), _p(L), _p(flags), nthreads))
         return dict(query=q, vertices=v, L=L, flags=flags)
+
+    def channels(self, density, temperature=None, albedo=None, aniso=None, nthreads=0):
+        """Per-tet channel means and voxel majorants (orc_grid_channels)."""
+        c = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
+        d, t, a_, g = c(density), c(temperature), c(albedo), c(aniso)
+        self._keep = (d, t, a_, g)
+        _check(lib().orc_grid_channels(self._h, _p(d), _p(t), _p(a_), _p(g), nthreads))
+
+    def export_channels(self):
+        n = self.info()["num_tets"]
+        chan = np.empty((n, 3), np.float32); vmaj = np.empty(n, np.float32)
+        _check(lib().orc_grid_export_channels(self._h, _p(chan), _p(vmaj)))
+        return chan, vmaj
+
+    def render_ext_paths(self, camera, medium, seed, px, py, sample, flags, emission_scale=0.0, density=None,
+                         nthreads=0):
+        """The extended estimator (emission, per-tet albedo / g, voxel medium with delta tracking)."""
+        px = np.ascontiguousarray(px, np.int32); py = np.ascontiguousarray(py, np.int32)
+        sm = np.ascontiguousarray(sample, np.int32)
+        n = len(px)
+        vox = np.ascontiguousarray(density, np.float32) if density is not None else None
+        ext = _Ext()
+        ext.flags = flags; ext.emission_scale = emission_scale
+        ext.density = vox.ctypes.data_as(C.c_void_p) if vox is not None else None
+        L = np.empty(n, np.float64); fl = np.empty(n, np.int32); coll = np.empty(n, np.int32)
+        steps = np.empty(n, np.int64)
+        _check(lib().orc_render_ext_paths(self._h, C.byref(camera_struct(camera)), C.byref(medium_struct(medium)),
+                                          C.byref(ext), C.c_uint64(seed), C.c_int64(n), _p(px), _p(py), _p(sm),
+                                          _p(L), _p(fl), _p(coll), _p(steps), nthreads))
+        return dict(L=L, flags=fl, collisions=coll, steps=steps)
 
     def render(self, camera, medium, spp, seed, sample_offset=0, nthreads=0):
         s = np.zeros((camera.height, camera.width), np.float64)

@@ -437,6 +437,10 @@ struct orc_grid {
   std::vector<std::array<float, 4>> plane;
   std::vector<float> rho, rho_max;
   std::unordered_map<uint64_t, int32_t> index_of_code;
+  // extra per-tet channels (orc_grid_channels): temperature, albedo, g; the voxel majorant
+  int channel_mask = 0;
+  std::vector<std::array<float, 3>> chan;
+  std::vector<float> vmaj;
 };
 
 namespace {
@@ -929,6 +933,146 @@ PathOut trace(const Cells& cells, const Domain& D, const Locate& locate_fn, cons
   return out;
 }
 
+// ============================================================================
+// Extra channels (Sec. 3: "extra channels for, e.g., temperature, albedo, phase
+// function parameters").  Per tet, the mean of each channel volume over D (the
+// same voxel set as the density), quantised like the density; g = 2 a - 1 from
+// an anisotropy volume a in [0, 1], clamped to [-0.99, 0.99].  The voxel
+// majorant of a tet bounds the voxel density anywhere in it: (max q + 1) / 2^24
+// over the voxels whose cells touch the tet's bounding box.
+// ============================================================================
+float channel_mean(const Stats& st) {
+  return (float)((double)st.sum / ((double)st.count * 16777216.0));
+}
+
+float voxel_majorant(const Volume& V, const Tet& T) {
+  const Domain& D = *V.D;
+  int64_t w = (int64_t)1 << (D.K - D.m);          // voxel edge in vertex units
+  int dims[3] = {D.nx, D.ny, D.nz};
+  int64_t lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    int64_t mn = T.x[0][a], mx = T.x[0][a];
+    for (int i = 1; i < 4; ++i) { mn = std::min<int64_t>(mn, T.x[i][a]); mx = std::max<int64_t>(mx, T.x[i][a]); }
+    lo[a] = std::max<int64_t>(0, floor_div(mn, w));
+    hi[a] = std::min<int64_t>(dims[a] - 1, floor_div(mx, w));
+  }
+  uint32_t m = 0;
+  for (int64_t k = lo[2]; k <= hi[2]; ++k)
+    for (int64_t j = lo[1]; j <= hi[1]; ++j)
+      for (int64_t i = lo[0]; i <= hi[0]; ++i) m = std::max(m, V.q[((size_t)k * D.ny + j) * D.nx + i]);
+  return (float)(((double)m + 1.0) / 16777216.0);
+}
+
+// The extended estimator.  flags: emission (1), per-tet albedo (2), per-tet g
+// (4), voxel medium with delta tracking (8).
+//  * emission: at every real collision the collision estimator of the emitted
+//    radiance, beta (1 - albedo) Le with Le = emission_scale * temperature;
+//  * voxel medium: the density at x is the voxel value of the voxel holding x
+//    (the regular-grid comparator's medium); free flights are tracked against
+//    the tet majorant (regular tracking in the majorant medium, then a tentative
+//    collision is real with probability rho(x) / majorant, decided in fp32 as
+//    u * majorant < rho(x)), shadow rays use ratio tracking, prod (1 - rho / majorant).
+//    Delta-tracking random numbers after a free flight's first: slots 2^20 + k,
+//    k the path's running count (distance, then acceptance, per tentative event).
+struct ExtSpec { int flags; double emission_scale; const float* voxel; };
+
+struct MajorantCells {
+  const orc_grid* G;
+  double sigma_unit;
+  double density(int32_t c) const { return (double)G->vmaj[c]; }
+  Exit exit(int32_t c, V3 o, V3 d, double t) const { TetCells tc = {G, sigma_unit}; return tc.exit(c, o, d, t); }
+};
+
+float voxel_density_at(const orc_grid* G, const float* vox, V3 x) {
+  const Domain& D = G->D;
+  double p[3] = {x.x, x.y, x.z};
+  int dims[3] = {D.nx, D.ny, D.nz};
+  int64_t idx[3];
+  for (int a = 0; a < 3; ++a) {
+    int64_t i = (int64_t)std::floor(p[a] * (double)D.n);
+    idx[a] = std::min<int64_t>(std::max<int64_t>(i, 0), dims[a] - 1);
+  }
+  return vox[((size_t)idx[2] * D.ny + idx[1]) * D.nx + idx[0]];
+}
+
+template <class Locate>
+PathOut trace_ext(const orc_grid* G, const ExtSpec& X, const Locate& locate_fn, const CamRay& cr,
+                  const orc_medium* med, uint64_t seed, int px, int py, int sample) {
+  const double sigma_unit = (double)med->sigma_scale * G->D.cube;
+  TetCells cells = {G, sigma_unit};
+  MajorantCells mcells = {G, sigma_unit};
+  const bool voxel = (X.flags & 8) != 0;
+  PathOut out = {0, 0, 0, 0, 0};
+  PathLog log = {nullptr, 0, 0, false, 0, 0};
+  uint32_t pixel = (uint32_t)(py * cr.W + px);
+  uint32_t nrng = 0;
+  auto draw = [&]() { return uniform(seed, pixel, (uint32_t)sample, (1u << 20) + nrng++); };
+  double u0 = uniform(seed, pixel, (uint32_t)sample, 0), u1 = uniform(seed, pixel, (uint32_t)sample, 1);
+  Ray ray = camera_ray(cr, px, py, u0, u1);
+  double L = 0, beta = 1;
+  V3 w_sun = normalize(mul(from_f(med->sun_dir), -1.0));
+  double t_in;
+  if (!intersect_grid(G->D, ray, &t_in)) { out.L = med->env_radiance; out.flags = 4; return out; }
+  ray.o = grid_intersection_point(ray, t_in);
+  int32_t cell = locate_fn(ray.o);
+  if (cell < 0) { out.flags = 16; return out; }
+  for (int b = 0;; ++b) {
+    double tau = sample_free_path(uniform(seed, pixel, sample, 2 + 3 * b));
+    V3 x;
+    int hit;
+    if (!voxel) {
+      hit = march_through_cells(cells, ray, &cell, tau, &x, &log);
+    } else {
+      for (;;) {
+        hit = march_through_cells(mcells, ray, &cell, tau, &x, &log);
+        if (hit != 1) break;
+        const float rx = voxel_density_at(G, X.voxel, x);
+        const float mj = G->vmaj[cell];
+        const float u = (float)draw();
+        if (u * mj < rx) break;                              // a real collision
+        ray.o = x;                                           // a null collision: fly on from x
+        tau = sample_free_path(draw());
+      }
+    }
+    if (hit < 0) { out.flags |= hit == ESTEPLIMIT_ ? 8 : 16; break; }
+    if (hit == 0) { L += beta * med->env_radiance; break; }
+    out.collisions++;
+    const std::array<float, 3>& ch = G->chan[cell];
+    const double albedo = (X.flags & 2) ? (double)ch[1] : (double)med->albedo;
+    const double g = (X.flags & 4) ? (double)ch[2] : (double)med->g;
+    if (X.flags & 1) L += beta * (1.0 - albedo) * X.emission_scale * (double)ch[0];
+    beta *= albedo;
+    double T;
+    Ray shadow = {x, w_sun};
+    if (!voxel) {
+      int st = transmittance(cells, shadow, cell, &T, &log);
+      if (st < 0) { out.flags |= st == ESTEPLIMIT_ ? 8 : 16; break; }
+    } else {
+      // ratio tracking towards the sun
+      T = 1.0;
+      int32_t sc = cell;
+      int st = 0;
+      for (;;) {
+        V3 xs;
+        st = march_through_cells(mcells, shadow, &sc, sample_free_path(draw()), &xs, &log);
+        if (st != 1) break;
+        T *= 1.0 - (double)voxel_density_at(G, X.voxel, xs) / (double)G->vmaj[sc];
+        shadow.o = xs;
+      }
+      if (st < 0) { out.flags |= st == ESTEPLIMIT_ ? 8 : 16; break; }
+    }
+    L += beta * hg_pdf(g, dot(ray.d, w_sun)) * med->sun_irradiance * T;
+    if (b + 1 >= med->max_bounces) { out.flags |= 2; break; }
+    ray.d = sample_phase_function(g, uniform(seed, pixel, sample, 3 + 3 * b),
+                                  uniform(seed, pixel, sample, 4 + 3 * b), ray.d);
+    ray.o = x;
+  }
+  out.L = L;
+  if (log.degenerate) out.flags |= 1;
+  out.steps = log.steps;
+  return out;
+}
+
 bool valid_camera(const orc_camera* c) {
   return c && c->width > 0 && c->height > 0 && c->fov_y_deg > 0 && c->fov_y_deg < 180;
 }
@@ -1047,6 +1191,64 @@ int orc_cache_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* 
     PathOut o = trace(cells, g->D, loc, cr, med, seed, px[i], py[i], sample[i], nullptr, 0, &io);
     if (L) L[i] = o.L;
     if (flags) flags[i] = o.flags;
+  }
+  return OK;
+}
+
+int orc_grid_channels(orc_grid* g, const float* density, const float* temperature, const float* albedo,
+                      const float* aniso, int32_t nthreads) {
+  if (!g || !density) return EINVAL_;
+  const Domain& D = g->D;
+  size_t N = g->tets.size();
+  g->chan.assign(N, {0.0f, 0.0f, 0.0f});
+  g->vmaj.assign(N, 0.0f);
+  const float* vols[3] = {temperature, albedo, aniso};
+  int nt = set_threads(nthreads);
+  for (int c = 0; c < 3; ++c) {
+    if (!vols[c]) continue;
+    Volume V;
+    quantise(vols[c], D, &V);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+    for (int64_t i = 0; i < (int64_t)N; ++i) {
+      float m = channel_mean(density_stats(V, g->tets[i]));
+      if (c == 2) m = (float)std::min(0.99, std::max(-0.99, 2.0 * (double)m - 1.0));
+      g->chan[i][c] = m;
+    }
+  }
+  Volume V;
+  quantise(density, D, &V);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+  for (int64_t i = 0; i < (int64_t)N; ++i) g->vmaj[i] = voxel_majorant(V, g->tets[i]);
+  g->channel_mask = (temperature ? 1 : 0) | (albedo ? 2 : 0) | (aniso ? 4 : 0) | 8;
+  return OK;
+}
+
+int orc_grid_export_channels(const orc_grid* g, float* chan, float* vmaj) {
+  if (!g || !g->channel_mask) return EINVAL_;
+  for (size_t i = 0; i < g->tets.size(); ++i) {
+    if (chan) for (int c = 0; c < 3; ++c) chan[3 * i + c] = g->chan[i][c];
+    if (vmaj) vmaj[i] = g->vmaj[i];
+  }
+  return OK;
+}
+
+int orc_render_ext_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* med, const orc_ext* ext,
+                         uint64_t seed, int64_t n, const int32_t* px, const int32_t* py, const int32_t* sample,
+                         double* L, int32_t* flags, int32_t* collisions, int64_t* steps, int32_t nthreads) {
+  if (!g || !valid_camera(cam) || !valid_medium(med) || !ext || n < 0) return EINVAL_;
+  int need = ext->flags & 15;
+  if ((need & ~g->channel_mask) || ((ext->flags & 8) && !ext->density)) return EINVAL_;
+  ExtSpec X = {ext->flags, (double)ext->emission_scale, ext->density};
+  CamRay cr = camera_rays(cam, g->D);
+  auto loc = [&](V3 p) { return locate(g, p); };
+  int nt = set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+  for (int64_t i = 0; i < n; ++i) {
+    PathOut o = trace_ext(g, X, loc, cr, med, seed, px[i], py[i], sample[i]);
+    if (L) L[i] = o.L;
+    if (flags) flags[i] = o.flags;
+    if (collisions) collisions[i] = o.collisions;
+    if (steps) steps[i] = o.steps;
   }
   return OK;
 }

@@ -77,6 +77,26 @@ int orc_render(const orc_grid* g, const orc_camera* cam, const orc_medium* med, 
                uint64_t seed, int32_t sample_offset, double* sum, double* sumsq, int64_t* steps,
                int32_t nthreads);
 
+/* Extra per-tet channels (Sec. 3): the mean over D (like the density) of a
+ * temperature, an albedo and an anisotropy volume (g = 2a - 1, clamped to
+ * +-0.99), each quantised like the density (NULL: channel absent), and the voxel
+ * majorant (max q + 1) / 2^24 over the voxels touching the tet's bounding box. */
+int orc_grid_channels(orc_grid* g, const float* density, const float* temperature, const float* albedo,
+                      const float* aniso, int32_t nthreads);
+/* chan float[N][3] (temperature, albedo, g), vmaj float[N]; either may be NULL. */
+int orc_grid_export_channels(const orc_grid* g, float* chan, float* vmaj);
+
+/* The extended estimator: flags 1 emission (collision estimator, Le =
+ * emission_scale * temperature), 2 per-tet albedo, 4 per-tet g, 8 voxel medium
+ * (density = the voxel holding x, from `density` [nz][ny][nx]) tracked against
+ * the tet majorants: delta tracking for free flights (acceptance decided in fp32
+ * as u * majorant < rho), ratio tracking for shadow rays; random slots 2^20 + k
+ * for the k-th delta-tracking draw of a path. */
+typedef struct { int32_t flags; float emission_scale; const float* density; } orc_ext;
+int orc_render_ext_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* med, const orc_ext* ext,
+                         uint64_t seed, int64_t n, const int32_t* px, const int32_t* py, const int32_t* sample,
+                         double* L, int32_t* flags, int32_t* collisions, int64_t* steps, int32_t nthreads);
+
 /* The regular-grid comparator: same estimator on the voxel grid (3D DDA). */
 int orc_dda_paths(const float* density, int32_t nx, int32_t ny, int32_t nz, const float box_min[3],
                   float voxel_size, const orc_camera* cam, const orc_medium* med, uint64_t seed,

@@ -371,3 +371,39 @@ def mlp_random_records(n: int, seed: int):
     r[:, 3] = rng.uniform(0, 2, n)
     r[:, 7] = (np.arange(n) % 8 != 7).astype(np.float32)
     return r
+
+
+def make_channels(s: Scene, device="cpu", z_range: Optional[Tuple[int, int]] = None):
+    """Extra channel volumes of a scene, float32[nz][ny][nx] each with values
+    q / 2**24 (integer-exact like the density): temperature (a hot core fading
+    outwards, broken up by fBm: the explosion-style asset), albedo in [0.5, 1]
+    and anisotropy a in [0.35, 0.95] (g = 2a - 1 in [-0.3, 0.9]), both from
+    low-frequency value noise."""
+    nx, ny, nz = s.dims
+    z0, z1 = z_range if z_range is not None else (0, nz)
+    shape = (z1 - z0, ny, nx)
+    temp = torch.empty(shape, dtype=torch.float32, device=device)
+    alb = torch.empty_like(temp)
+    ani = torch.empty_like(temp)
+    n_ref = max(s.dims)
+    slab = max(1, (1 << 22) // (nx * ny))
+    for a in range(z0, z1, slab):
+        b = min(z1, a + slab)
+        i, j, k = _grid_idx(a, b, ny, nx, device)
+        dx, dy, dz = 2 * i + 1 - nx, 2 * j + 1 - ny, 2 * k + 1 - nz
+        r2 = (dx * dx * ONE16) // (nx * nx) + (dy * dy * ONE16) // (ny * ny) + (dz * dz * ONE16) // (nz * nz)
+        core = torch.clamp(ONE16 - (r2 * 4) // 3, 0, ONE16)                    # 1 - r^2 / 0.75 (r in box units)
+        X, Y, Z = (_coords_from_index(i, n_ref, nx, 4), _coords_from_index(j, n_ref, ny, 4),
+                   _coords_from_index(k, n_ref, nz, 4))
+        f = fbm(X, Y, Z, 4, s.volume_seed + 31)
+        t16 = (core * f) >> 16                                               # [0, 2^16)
+        temp[a - z0:b - z0] = ((t16 << 8).to(torch.float64) / ONE24).to(torch.float32)
+        L1 = (_coords_from_index(i, n_ref, nx, 2), _coords_from_index(j, n_ref, ny, 2),
+              _coords_from_index(k, n_ref, nz, 2))
+        va = value_noise(*L1, s.volume_seed + 57)                              # [0, 65535]
+        vg = value_noise(*L1, s.volume_seed + 83)
+        qa = (ONE24 >> 1) + (va << 7)                                          # 0.5 + va / 2^17 * ... in [0.5, 1)
+        qg = (ONE24 * 35) // 100 + ((vg * ((ONE24 * 60) // 100)) >> 16)        # [0.35, 0.95)
+        alb[a - z0:b - z0] = (qa.to(torch.float64) / ONE24).to(torch.float32)
+        ani[a - z0:b - z0] = (qg.to(torch.float64) / ONE24).to(torch.float32)
+    return temp, alb, ani
