@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-dda", action="store_true", help="skip the regular-grid comparator frame")
     p.add_argument("--cpu-sample-px", type=int, default=0, help="side of the oracle's pixel window (0: auto)")
     p.add_argument("--no-cache", action="store_true", help="skip the radiance-cache time-to-equal-RMSE leg")
+    p.add_argument("--no-ext", action="store_true", help="skip the extra-channel / voxel-medium frames")
     p.add_argument("--cache-train-rounds", default="8,32,128", help="training budgets (rounds of 2^16 samples)")
     p.add_argument("--cache-ref-pixels", type=int, default=4096)
     p.add_argument("--cache-ref-spp", type=int, default=4096)
@@ -243,6 +244,9 @@ def run_ours(args):
     cache = None
     if not args.no_cache and rank == 0:
         cache = cache_leg(args, s, grid, dev, ms_per_step)
+    ext = None
+    if not args.no_ext and rank == 0:
+        ext = ext_leg(s, grid, vol, dev, comparator)
 
     # end to end through the public API: host volume -> device, build, render, image -> host
     e2e = None
@@ -303,10 +307,54 @@ def run_ours(args):
                            "l2": "inputs larger than L2: grid records %.2f GB" % (ntets * 32 / 1e9),
                            "parallelism": "one frame per rank, disjoint sample ranges"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clk, "comparator": comparator, "cache": cache}
+                "clocks": clk, "comparator": comparator, "cache": cache, "ext": ext}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# extra channels (temperature -> emission, albedo, g) and the voxel medium
+# ---------------------------------------------------------------------------
+def ext_leg(s, grid, vol, dev, comparator):
+    """Frames of the extended medium on the same grid: per-cell channels with
+    emission, and the voxel medium tracked against the cells' voxel majorants
+    (the medium the regular-grid comparator renders)."""
+    import torch
+    import paper_2506_11510_gb300 as tv
+    from paper_2506_11510_gb300 import workloads as W
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        out = fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    t, a, g = W.make_channels(s, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    grid.channels(vol, t, a, g)
+    chan_ms = (time.time() - t0) * 1e3
+    del t, a, g
+    paths = s.camera.width * s.camera.height * s.spp
+    res = {"channels_ms": round(chan_ms, 1), "variants": []}
+    for name, flags in (("emission+albedo+g channels", 7), ("voxel medium, delta tracking on tet majorants", 8),
+                        ("voxel medium + channels", 15)):
+        tv.tet_render_ext(grid, s.camera, s.medium, flags, s.spp, s.render_seed, emission_scale=2.0, density=vol)
+        stats = tv.new_stats(dev)
+        _, ms = timed(lambda: tv.tet_render_ext(grid, s.camera, s.medium, flags, s.spp, s.render_seed,
+                                                emission_scale=2.0, density=vol, stats=stats))
+        c = tv.stats_dict(stats)
+        v = {"flags": flags, "name": name, "ms_per_frame": round(ms, 2), "mpaths_s": round(paths / ms / 1e3, 3),
+             "tet_steps_per_path": round((c["tet_steps"] + c["shadow_steps"]) / paths, 1),
+             "collisions_per_path": round(c["collisions"] / paths, 3)}
+        if flags & 8 and comparator is not None:
+            v["speedup_vs_dda_same_medium"] = round(comparator["ms_per_frame"] / ms, 3)
+        res["variants"].append(v)
+    return res
 
 
 # ---------------------------------------------------------------------------

@@ -218,6 +218,54 @@ int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const tg_medium* 
                        int32_t sample_offset, float* accum_sum, float* accum_sumsq, void* cuda_stream);
 
 /* ==========================================================================
+ * Extra channels and the voxel medium.  Sec. 3: the grid "supports extra
+ * channels for, e.g., temperature, albedo, phase function parameters"; the
+ * explosion of the paper's last figure has density and temperature.
+ * ========================================================================== */
+
+/*
+ * tg_grid_channels - per-cell channels of a grid built by leb_build (not of an
+ * imported grid: TG_EINVAL): for each of temperature, albedo and anisotropy
+ * a (device float[nz][ny][nx] on the grid's voxel lattice, values in [0, 1],
+ * NULL = absent), the mean over the cell's D (the voxels whose centres lie in
+ * the closed cell, else the centroid's voxel), quantised like the density
+ * (round(v 2^24)); the phase parameter is g = 2a - 1 clamped to [-0.99, 0.99].
+ * Also the cell's voxel majorant (max q + 1) / 2^24 over the voxels of
+ * `density` touching the cell's bounding box: at least the voxel density
+ * anywhere in the cell.  Replaces earlier channels.  Synchronous.
+ */
+int tg_grid_channels(tg_grid* g, const float* density, const float* temperature, const float* albedo,
+                     const float* aniso, void* cuda_stream);
+/* chan: device float[N][4] (temperature, albedo, g, 0), vmaj: device float[N]; NULL allowed. */
+int tg_grid_export_channels(const tg_grid* g, float* chan, float* vmaj, void* cuda_stream);
+
+enum { TG_EXT_EMISSION = 1, TG_EXT_ALBEDO = 2, TG_EXT_G = 4, TG_EXT_VOXEL = 8 };
+/* The extended medium of a render (flags are ORed; channels must have been computed):
+ *  EMISSION: at every real collision the path adds beta (1 - albedo) Le, Le =
+ *    emission_scale * temperature of the cell (collision estimator of emission);
+ *  ALBEDO, G: the cell's albedo / g replace the medium's;
+ *  VOXEL: the medium is `density` (device float[nz][ny][nx], the grid's voxel
+ *    lattice): the density at x is the voxel holding x.  Free flights are
+ *    tracked against the cells' voxel majorants (delta tracking: a tentative
+ *    collision is real when u * majorant < rho(x), in fp32), shadow rays by
+ *    ratio tracking; the k-th such draw of the free flight (shadow ray) of
+ *    bounce b uses Philox counter (s, k / 4, 1 + 2b (2 + 2b), 0), word k % 4. */
+typedef struct {
+  int32_t flags;
+  float emission_scale;
+  const float* density;
+} tg_ext;
+
+/* tet_render / tet_trace_paths with the extended medium (same arguments and
+ * semantics otherwise; the trace variant has no visited-cell output). */
+int tet_render_ext(const tg_grid* g, const tg_camera* cam, const tg_medium* med, const tg_ext* ext, int32_t spp,
+                   uint64_t seed, int32_t sample_offset, float* accum_sum, float* accum_sumsq, tg_stats* stats,
+                   void* cuda_stream);
+int tet_trace_ext_paths(const tg_grid* g, const tg_camera* cam, const tg_medium* med, const tg_ext* ext,
+                        uint64_t seed, int64_t n, const int32_t* px, const int32_t* py, const int32_t* sample,
+                        float* L, int32_t* flags, int32_t* collisions, int64_t* steps, void* cuda_stream);
+
+/* ==========================================================================
  * Learned radiance cache.  A small MLP R(x, d) ends paths after one or two
  * collisions: it stands for the radiance that the rest of a path brings back,
  * is trained online on the tracer's own path vertices, and the plain tracer

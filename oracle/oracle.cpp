@@ -68,11 +68,13 @@ void philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
 }
 
 // Random number of a path: key = (seed lo, seed hi ^ pixel), counter =
-// (sample, slot / 4, 0, 0), word slot % 4; u = (word >> 8) * 2^-24 in [0, 1).
-// Slots: 0, 1 pixel jitter; 2 + 3b free path of bounce b; 3 + 3b, 4 + 3b phase.
-double uniform(uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t slot) {
+// (sample, slot / 4, stream, 0), word slot % 4; u = (word >> 8) * 2^-24 in [0, 1).
+// Stream 0: 0, 1 pixel jitter; 2 + 3b free path of bounce b; 3 + 3b, 4 + 3b phase.
+// Streams 1 + 2b and 2 + 2b: the k-th delta-tracking draw of the free flight and
+// of the shadow ray of bounce b (slot k).
+double uniform(uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t slot, uint32_t stream = 0) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ pixel};
-  uint32_t ctr[4] = {sample, slot / 4, 0, 0};
+  uint32_t ctr[4] = {sample, slot / 4, stream, 0};
   uint32_t out[4];
   philox(ctr, key, out);
   return (double)(out[slot % 4] >> 8) * (1.0 / 16777216.0);
@@ -972,8 +974,9 @@ float voxel_majorant(const Volume& V, const Tet& T) {
 //    the tet majorant (regular tracking in the majorant medium, then a tentative
 //    collision is real with probability rho(x) / majorant, decided in fp32 as
 //    u * majorant < rho(x)), shadow rays use ratio tracking, prod (1 - rho / majorant).
-//    Delta-tracking random numbers after a free flight's first: slots 2^20 + k,
-//    k the path's running count (distance, then acceptance, per tentative event).
+//    Delta-tracking random numbers (acceptance, then the next free path, per
+//    tentative collision; free paths of a shadow ray): slot k of stream 1 + 2b
+//    (free flight of bounce b) or 2 + 2b (its shadow ray), k counted per segment.
 struct ExtSpec { int flags; double emission_scale; const float* voxel; };
 
 struct MajorantCells {
@@ -1005,8 +1008,8 @@ PathOut trace_ext(const orc_grid* G, const ExtSpec& X, const Locate& locate_fn, 
   PathOut out = {0, 0, 0, 0, 0};
   PathLog log = {nullptr, 0, 0, false, 0, 0};
   uint32_t pixel = (uint32_t)(py * cr.W + px);
-  uint32_t nrng = 0;
-  auto draw = [&]() { return uniform(seed, pixel, (uint32_t)sample, (1u << 20) + nrng++); };
+  uint32_t kseg = 0;                                  // draws of the current segment
+  auto draw = [&](uint32_t stream) { return uniform(seed, pixel, (uint32_t)sample, kseg++, stream); };
   double u0 = uniform(seed, pixel, (uint32_t)sample, 0), u1 = uniform(seed, pixel, (uint32_t)sample, 1);
   Ray ray = camera_ray(cr, px, py, u0, u1);
   double L = 0, beta = 1;
@@ -1020,6 +1023,7 @@ PathOut trace_ext(const orc_grid* G, const ExtSpec& X, const Locate& locate_fn, 
     double tau = sample_free_path(uniform(seed, pixel, sample, 2 + 3 * b));
     V3 x;
     int hit;
+    kseg = 0;
     if (!voxel) {
       hit = march_through_cells(cells, ray, &cell, tau, &x, &log);
     } else {
@@ -1028,10 +1032,10 @@ PathOut trace_ext(const orc_grid* G, const ExtSpec& X, const Locate& locate_fn, 
         if (hit != 1) break;
         const float rx = voxel_density_at(G, X.voxel, x);
         const float mj = G->vmaj[cell];
-        const float u = (float)draw();
+        const float u = (float)draw(1u + 2u * b);
         if (u * mj < rx) break;                              // a real collision
         ray.o = x;                                           // a null collision: fly on from x
-        tau = sample_free_path(draw());
+        tau = sample_free_path(draw(1u + 2u * b));
       }
     }
     if (hit < 0) { out.flags |= hit == ESTEPLIMIT_ ? 8 : 16; break; }
@@ -1052,9 +1056,10 @@ PathOut trace_ext(const orc_grid* G, const ExtSpec& X, const Locate& locate_fn, 
       T = 1.0;
       int32_t sc = cell;
       int st = 0;
+      kseg = 0;
       for (;;) {
         V3 xs;
-        st = march_through_cells(mcells, shadow, &sc, sample_free_path(draw()), &xs, &log);
+        st = march_through_cells(mcells, shadow, &sc, sample_free_path(draw(2u + 2u * b)), &xs, &log);
         if (st != 1) break;
         T *= 1.0 - (double)voxel_density_at(G, X.voxel, xs) / (double)G->vmaj[sc];
         shadow.o = xs;

@@ -90,8 +90,9 @@ int orc_grid_export_channels(const orc_grid* g, float* chan, float* vmaj);
  * emission_scale * temperature), 2 per-tet albedo, 4 per-tet g, 8 voxel medium
  * (density = the voxel holding x, from `density` [nz][ny][nx]) tracked against
  * the tet majorants: delta tracking for free flights (acceptance decided in fp32
- * as u * majorant < rho), ratio tracking for shadow rays; random slots 2^20 + k
- * for the k-th delta-tracking draw of a path. */
+ * as u * majorant < rho), ratio tracking for shadow rays; the k-th such draw of
+ * the free flight (shadow ray) of bounce b is slot k of Philox stream 1 + 2b
+ * (2 + 2b): counter (sample, k / 4, stream, 0). */
 typedef struct { int32_t flags; float emission_scale; const float* density; } orc_ext;
 int orc_render_ext_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* med, const orc_ext* ext,
                          uint64_t seed, int64_t n, const int32_t* px, const int32_t* py, const int32_t* sample,

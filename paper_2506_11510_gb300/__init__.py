@@ -5,11 +5,12 @@ The computation lives in libtetvol.so (CUDA, sm_103a, C ABI in include/tetvol.h)
 this package builds it in-tree and binds it with ctypes.
 """
 from .api import (Grid, GridInfo, build_scene_grid, grid_import, grid_render, grid_trace_paths, leb_build,
-                  new_stats, stats_dict, tet_optical_depth, tet_render, tet_trace_paths)
+                  new_stats, stats_dict, tet_optical_depth, tet_render, tet_render_ext, tet_trace_ext_paths,
+                  tet_trace_paths)
 from ._native import TetvolError
 from . import cache
 from .cache import RadianceCache
 
 __all__ = ["Grid", "GridInfo", "TetvolError", "build_scene_grid", "grid_import", "grid_render", "grid_trace_paths",
-           "leb_build", "new_stats", "stats_dict", "tet_optical_depth", "tet_render", "tet_trace_paths", "cache",
+           "leb_build", "new_stats", "stats_dict", "tet_optical_depth", "tet_render", "tet_trace_paths", "tet_render_ext", "tet_trace_ext_paths", "cache",
            "RadianceCache"]

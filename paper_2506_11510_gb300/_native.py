@@ -30,6 +30,10 @@ class TgVolumeDesc(C.Structure):
                 ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
 
 
+class TgExt(C.Structure):
+    _fields_ = [("flags", C.c_int32), ("emission_scale", C.c_float), ("density", C.c_void_p)]
+
+
 STATS_FIELDS = ("paths", "tet_steps", "shadow_steps", "collisions", "escapes", "truncated", "step_limit", "misses")
 
 # name -> (restype, argtypes)
@@ -53,6 +57,12 @@ SIGNATURES = {
     "tet_optical_depth": (C.c_int, [_VP, _I64, _VP, _VP, _F, _VP, _VP, _VP, _I32, _VP, _VP]),
     "tet_render_noalloc": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _I32, _U64, _I32, _VP, _VP,
                                      _VP]),
+    "tg_grid_channels": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "tg_grid_export_channels": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "tet_render_ext": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), C.POINTER(TgExt), _I32, _U64, _I32,
+                                 _VP, _VP, _VP, _VP]),
+    "tet_trace_ext_paths": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), C.POINTER(TgExt), _U64, _I64,
+                                      _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "tg_random_paths": (C.c_int, [_U64, _I64, _I32, _I32, _I32, _VP, _VP, _VP, _VP]),
     "tet_cache_samples": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _U64, _I64, _VP, _VP, _VP, _I32,
                                     _VP, _VP, _VP]),

@@ -118,6 +118,34 @@ class Grid:
         return out
 
 
+    def channels(self, density: torch.Tensor, temperature=None, albedo=None, aniso=None):
+        """Per-cell channel means and voxel majorants (tg_grid_channels)."""
+        for t, nm in ((density, "density"), (temperature, "temperature"), (albedo, "albedo"), (aniso, "aniso")):
+            if t is not None:
+                _need(t, torch.float32, nm, (self.desc.nz, self.desc.ny, self.desc.nx))
+        N.check(N.lib().tg_grid_channels(self._h, _ptr(density), _ptr(temperature), _ptr(albedo), _ptr(aniso),
+                                         _stream()), "tg_grid_channels")
+
+    def export_channels(self):
+        n = self.info.num_tets
+        dev = torch.device("cuda", torch.cuda.current_device())
+        chan = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        vmaj = torch.empty(n, dtype=torch.float32, device=dev)
+        N.check(N.lib().tg_grid_export_channels(self._h, _ptr(chan), _ptr(vmaj), _stream()),
+                "tg_grid_export_channels")
+        return chan, vmaj
+
+
+def ext_struct(flags: int, emission_scale: float = 0.0, density: Optional[torch.Tensor] = None) -> N.TgExt:
+    x = N.TgExt()
+    x.flags = int(flags)
+    x.emission_scale = float(emission_scale)
+    if density is not None:
+        _need(density, torch.float32, "density")
+    x.density = _ptr(density).value if density is not None else None
+    return x
+
+
 def leb_build(density: torch.Tensor, box_min, voxel_size, camera=None, footprint_px: float = 0.0,
               variation_threshold: float = -1.0, max_depth: int = 12, density_format: int = 0) -> Grid:
     """Sec. 2: build the adaptive conforming LEB grid of a density volume float32[nz][ny][nx]."""
@@ -254,4 +282,34 @@ def tet_optical_depth(grid: Grid, origins: torch.Tensor, dirs: torch.Tensor, sig
     N.check(N.lib().tet_optical_depth(grid.handle, n, _ptr(origins), _ptr(dirs), float(sigma), _ptr(out["tau"]),
                                       _ptr(out["steps"]), _ptr(seq), int(seq_cap), _ptr(seq_len), _stream()),
             "tet_optical_depth")
+    return out
+
+
+def tet_render_ext(grid: Grid, camera, medium, flags: int, spp: int, seed: int, emission_scale: float = 0.0,
+                   density: Optional[torch.Tensor] = None, sample_offset: int = 0, accum_sum=None, accum_sumsq=None,
+                   stats: Optional[torch.Tensor] = None, want_sq: bool = True):
+    """tet_render with the extended medium: per-cell emission / albedo / g, or the voxel
+    medium `density` tracked against the cells' voxel majorants (flags TG_EXT_*)."""
+    s, s2 = _accum(camera, accum_sum, accum_sumsq, want_sq)
+    if stats is not None:
+        _need(stats, torch.int64, "stats", (len(N.STATS_FIELDS),))
+    x = ext_struct(flags, emission_scale, density)
+    N.check(N.lib().tet_render_ext(grid.handle, C.byref(camera_struct(camera)), C.byref(medium_struct(medium)),
+                                   C.byref(x), int(spp), C.c_uint64(seed), int(sample_offset), _ptr(s), _ptr(s2),
+                                   _ptr(stats), _stream()), "tet_render_ext")
+    return s, s2
+
+
+def tet_trace_ext_paths(grid: Grid, camera, medium, flags: int, seed: int, px, py, sample, emission_scale=0.0,
+                        density: Optional[torch.Tensor] = None) -> dict:
+    px, py, sm, dev = _paths(px, py, sample)
+    n = px.numel()
+    out = dict(L=torch.empty(n, dtype=torch.float32, device=dev), flags=torch.empty(n, dtype=torch.int32, device=dev),
+               collisions=torch.empty(n, dtype=torch.int32, device=dev),
+               steps=torch.empty(n, dtype=torch.int64, device=dev))
+    x = ext_struct(flags, emission_scale, density)
+    N.check(N.lib().tet_trace_ext_paths(grid.handle, C.byref(camera_struct(camera)), C.byref(medium_struct(medium)),
+                                        C.byref(x), C.c_uint64(seed), n, _ptr(px), _ptr(py), _ptr(sm),
+                                        _ptr(out["L"]), _ptr(out["flags"]), _ptr(out["collisions"]),
+                                        _ptr(out["steps"]), _stream()), "tet_trace_ext_paths")
     return out

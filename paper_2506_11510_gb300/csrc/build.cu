@@ -67,7 +67,7 @@ struct Leaves {
   size_t cap = 0;
   void ensure(size_t n) {
     if (n <= cap) return;
-    size_t c = std::max<size_t>(n + n / 2, 1024);
+    size_t c = std::max<size_t>(2 * n, 1024);
     v.alloc(3 * c); code.alloc(c); sum.alloc(c); tag.alloc(c); crit.alloc(c); cnt.alloc(c); mn.alloc(c); mx.alloc(c);
     cap = c;
   }
@@ -253,6 +253,23 @@ __device__ __forceinline__ void tet_box(const int x[4][3], const Geo& g, int lo[
   }
 }
 
+// Voxel box of a leaf: the voxels whose centres lie in the tet's bounding box,
+// or (BOX) every voxel whose cell touches the bounding box.
+template <bool BOX>
+__device__ __forceinline__ void leaf_box(const int x[4][3], const Geo& g, int lo[3], int hi[3]) {
+  if (!BOX) { tet_box(x, g, lo, hi); return; }
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  const int w = 2 * g.h;                           // voxel edge in vertex units
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int mn = x[0][a], mx = x[0][a];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) { mn = min(mn, x[k][a]); mx = max(mx, x[k][a]); }
+    lo[a] = max(0, mn / w);                        // coordinates are non-negative
+    hi[a] = min(dims[a] - 1, mx / w);
+  }
+}
+
 // A box of at most 32 rows of at most 32 voxels: one thread scans it.
 __device__ __forceinline__ bool small_box(const int lo[3], const int hi[3]) {
   return (long long)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) <= 32 && hi[0] - lo[0] < 32;
@@ -282,13 +299,14 @@ __device__ __forceinline__ void row_interval(const int nrm[4][3], const long lon
 
 // A3 statistics, pass 1: work items of the new leaves (ROWS rows of the leaf's
 // voxel box each); reset their statistics
+template <bool BOX>
 __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo g, unsigned long long* chunks) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   const long long i = list ? list[j] : j;
   int x[4][3], lo[3], hi[3];
   load_tet(L.v, i, x);
-  tet_box(x, g, lo, hi);
+  leaf_box<BOX>(x, g, lo, hi);
   long long rows = 0;
   if (hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2])
     rows = (long long)(hi[1] - lo[1] + 1) * (long long)(hi[2] - lo[2] + 1);
@@ -301,6 +319,7 @@ __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo
 // (along x) of a leaf's voxel box, one row interval per lane (row_interval), so
 // only the voxels inside are read: by the whole warp along each row in turn when
 // the box is at least 32 voxels wide (coalesced), else by each lane along its row.
+template <bool BOX>
 __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long* list, long long m,
                                                     const unsigned long long* chunk_off, unsigned long long total,
                                                     const uint32_t* __restrict__ q, Geo g) {
@@ -318,11 +337,13 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long*
     const long long i = list ? list[j] : j;
     int x[4][3], lo[3], hi[3];
     load_tet(L.v, i, x);
-    tet_box(x, g, lo, hi);
+    leaf_box<BOX>(x, g, lo, hi);
     int nrm[4][3];
     long long rhs[4];
+    if (!BOX) {
 #pragma unroll
-    for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
+      for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
+    }
     const long long wy = hi[1] - lo[1] + 1;
     const long long rows = wy * (hi[2] - lo[2] + 1);
     const long long r = ((long long)c - (long long)chunk_off[j]) * ROWS + lane;
@@ -332,7 +353,8 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long*
     long long rowoff = 0;
     if (r < rows) {
       const int jj = lo[1] + (int)(r % wy), kk = lo[2] + (int)(r / wy);
-      row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
+      if (BOX) { xa = lo[0]; xb = hi[0]; }
+      else row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
       rowoff = ((long long)kk * g.ny + jj) * g.nx;
     }
     if (hi[0] - lo[0] >= 31) {
@@ -366,6 +388,80 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long*
       atomicMax(L.mx + i, mx);
     }
   }
+}
+
+// Statistics of a leaf whose box is small (small_box), by one thread; other
+// leaves are left to k_stats_scan.
+template <bool BOX>
+__device__ __forceinline__ void small_leaf_stats(LeafPtrs L, long long i, const int x[4][3],
+                                                 const uint32_t* __restrict__ q, const Geo& g) {
+  int lo[3], hi[3];
+  leaf_box<BOX>(x, g, lo, hi);
+  if (!(hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2] && small_box(lo, hi))) return;
+  int nrm[4][3];
+  long long rhs[4];
+  if (!BOX) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
+  }
+  const int hs = g.K - g.m - 1;
+  uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
+  unsigned long long sum = 0;
+  for (int kk = lo[2]; kk <= hi[2]; ++kk)
+    for (int jj = lo[1]; jj <= hi[1]; ++jj) {
+      int xa = lo[0], xb = hi[0];
+      if (!BOX) row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
+      const uint32_t* row = q + ((size_t)kk * g.ny + jj) * g.nx;
+      for (int ii = xa; ii <= xb; ++ii) {
+        const uint32_t v = __ldg(row + ii);
+        ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+      }
+    }
+  L.cnt[i] = cnt; L.sum[i] = sum; L.mn[i] = mn; L.mx[i] = mx;
+}
+
+template <bool BOX>
+__global__ void k_leaf_small(LeafPtrs L, long long m, const uint32_t* __restrict__ q, Geo g) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int x[4][3];
+  load_tet(L.v, i, x);
+  small_leaf_stats<BOX>(L, i, x, q, g);
+}
+
+// Per-tet channel c of the final grid: the mean of the quantised channel over D
+// (the voxel of the centroid if D is empty), as the density; g = 2a - 1 in
+// [-0.99, 0.99] for the anisotropy channel.
+__global__ void k_channel_store(LeafPtrs L, long long m, const uint32_t* __restrict__ q, Geo g, int c,
+                                float* __restrict__ chan) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  unsigned long long sum = L.sum[i];
+  uint32_t cnt = L.cnt[i];
+  if (cnt == 0) {
+    int x[4][3];
+    load_tet(L.v, i, x);
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    int idx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long s4 = (long long)x[0][a] + x[1][a] + x[2][a] + x[3][a];
+      const long long v = s4 >> (g.K + 2 - g.m);
+      idx[a] = (int)(v < 0 ? 0 : (v > dims[a] - 1 ? dims[a] - 1 : v));
+    }
+    sum = q[((size_t)idx[2] * g.ny + idx[1]) * g.nx + idx[0]];
+    cnt = 1;
+  }
+  float mean = (float)((double)sum / ((double)cnt * 16777216.0));
+  if (c == 2) mean = (float)fmin(0.99, fmax(-0.99, 2.0 * (double)mean - 1.0));
+  chan[4 * i + c] = mean;
+}
+
+// Voxel majorant of every final tet: (max q + 1) / 2^24 over the voxels touching its box
+__global__ void k_vmaj_store(LeafPtrs L, long long m, float* __restrict__ vmaj) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  vmaj[i] = (float)(((double)L.mx[i] + 1.0) / 16777216.0);
 }
 
 // Sec. 2 criterion 2 in fp64 with every product and sum rounded on its own.
@@ -419,30 +515,7 @@ __global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, c
   int x[4][3];
   load_tet(L.v, i, x);
   const Geo& g = C.g;
-  {
-    int lo[3], hi[3];
-    tet_box(x, g, lo, hi);
-    if (hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2] && small_box(lo, hi)) {
-      int nrm[4][3];
-      long long rhs[4];
-#pragma unroll
-      for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
-      const int hs = g.K - g.m - 1;
-      uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
-      unsigned long long sum = 0;
-      for (int kk = lo[2]; kk <= hi[2]; ++kk)
-        for (int jj = lo[1]; jj <= hi[1]; ++jj) {
-          int xa, xb;
-          row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
-          const uint32_t* row = q + ((size_t)kk * g.ny + jj) * g.nx;
-          for (int ii = xa; ii <= xb; ++ii) {
-            const uint32_t v = __ldg(row + ii);
-            ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
-          }
-        }
-      L.cnt[i] = cnt; L.sum[i] = sum; L.mn[i] = mn; L.mx[i] = mx;
-    }
-  }
+  small_leaf_stats<false>(L, i, x, q, g);
   if (L.cnt[i] == 0) {
     const int dims[3] = {g.nx, g.ny, g.nz};
     int idx[3];
@@ -666,7 +739,7 @@ void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const u
   LeafPtrs L = Lv.ptrs();
   chunks.ensure(m + 1);
   off.ensure(m + 1);
-  k_stats_prep<<<blocks_for(m), TPB, 0, st>>>(L, list, m, C.g, chunks.p);
+  k_stats_prep<false><<<blocks_for(m), TPB, 0, st>>>(L, list, m, C.g, chunks.p);
   TV_LAUNCH();
   TV_CUDA(cudaMemsetAsync(chunks.p + m, 0, sizeof(unsigned long long), st));
   scan.exclusive(chunks.p, off.p, m + 1, st);
@@ -675,7 +748,7 @@ void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const u
   TV_CUDA(cudaStreamSynchronize(st));
   if (total) {
     const long long wblocks = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
-    k_stats_scan<<<(unsigned)wblocks, TPB, 0, st>>>(L, list, m, off.p, total, q, C.g);
+    k_stats_scan<false><<<(unsigned)wblocks, TPB, 0, st>>>(L, list, m, off.p, total, q, C.g);
     TV_LAUNCH();
   }
   k_stats_finish<<<blocks_for(m), TPB, 0, st>>>(L, list, m, q, C);
@@ -877,7 +950,103 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   return TG_OK;
 }
 
+// Per-tet channels and voxel majorants of a built grid (see tg_grid_channels).
+int grid_channels(GridImpl& G, const float* density, const float* temperature, const float* albedo,
+                  const float* aniso, cudaStream_t st) {
+  if (!G.verts || G.n == 0) return TG_EINVAL;
+  Geo g;
+  g.nx = G.nvox[0]; g.ny = G.nvox[1]; g.nz = G.nvox[2];
+  g.n = G.n_per_cube;
+  int m = 0;
+  while ((1 << m) < g.n) ++m;
+  g.m = m;
+  g.K = G.K;
+  g.max_depth = G.max_depth;
+  for (int a = 0; a < 3; ++a) g.C[a] = G.C[a];
+  g.h = 1 << (g.K - m - 1);
+  int dev = 0, sms = 0;
+  TV_CUDA(cudaGetDevice(&dev));
+  TV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long N = G.n;
+  const long long nvox = (long long)g.nx * g.ny * g.nz;
+  DevBuf<uint32_t> q(nvox), cnt(N), mn(N), mx(N);
+  DevBuf<unsigned long long> sum(N), chunks, off;
+  DevBuf<float> chan((size_t)N * 4), vmaj(N);
+  TV_CUDA(cudaMemsetAsync(chan.p, 0, (size_t)N * 16, st));
+  LeafPtrs L{reinterpret_cast<int4*>(G.verts), G.codes, nullptr, cnt.p, mn.p, mx.p, sum.p, nullptr};
+  Scanner scan;
+  const unsigned qblocks = (unsigned)std::min<long long>(blocks_for(nvox), (long long)sms * 32);
+  auto leaf_stats = [&](bool box) {
+    chunks.ensure(N + 1);
+    off.ensure(N + 1);
+    if (box) k_stats_prep<true><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p);
+    else k_stats_prep<false><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p);
+    TV_LAUNCH();
+    TV_CUDA(cudaMemsetAsync(chunks.p + N, 0, sizeof(unsigned long long), st));
+    scan.exclusive(chunks.p, off.p, N + 1, st);
+    unsigned long long total = 0;
+    TV_CUDA(cudaMemcpyAsync(&total, off.p + N, sizeof total, cudaMemcpyDeviceToHost, st));
+    TV_CUDA(cudaStreamSynchronize(st));
+    if (total) {
+      const long long wb = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
+      if (box) k_stats_scan<true><<<(unsigned)wb, TPB, 0, st>>>(L, nullptr, N, off.p, total, q.p, g);
+      else k_stats_scan<false><<<(unsigned)wb, TPB, 0, st>>>(L, nullptr, N, off.p, total, q.p, g);
+      TV_LAUNCH();
+    }
+    if (box) k_leaf_small<true><<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g);
+    else k_leaf_small<false><<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g);
+    TV_LAUNCH();
+  };
+  const float* vols[3] = {temperature, albedo, aniso};
+  int mask = 8;
+  for (int c = 0; c < 3; ++c) {
+    if (!vols[c]) continue;
+    k_quantize<<<qblocks, TPB, 0, st>>>(vols[c], q.p, nvox);
+    TV_LAUNCH();
+    leaf_stats(false);
+    k_channel_store<<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g, c, chan.p);
+    TV_LAUNCH();
+    mask |= 1 << c;
+  }
+  k_quantize<<<qblocks, TPB, 0, st>>>(density, q.p, nvox);
+  TV_LAUNCH();
+  leaf_stats(true);
+  k_vmaj_store<<<blocks_for(N), TPB, 0, st>>>(L, N, vmaj.p);
+  TV_LAUNCH();
+  TV_CUDA(cudaStreamSynchronize(st));
+  if (G.chan) cudaFree(G.chan);
+  if (G.vmaj) cudaFree(G.vmaj);
+  G.chan = reinterpret_cast<float4*>(chan.release());
+  G.vmaj = vmaj.release();
+  G.chan_mask = mask;
+  return TG_OK;
+}
+
 }  // namespace tv
+
+extern "C" int tg_grid_channels(tg_grid* g, const float* density, const float* temperature, const float* albedo,
+                                const float* aniso, void* cuda_stream) {
+  if (!g || !density) return TG_EINVAL;
+  try {
+    return tv::grid_channels(g->impl, density, temperature, albedo, aniso, (cudaStream_t)cuda_stream);
+  } catch (const tv::Error& e) {
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    return TG_ENOMEM;
+  }
+}
+
+extern "C" int tg_grid_export_channels(const tg_grid* g, float* chan, float* vmaj, void* cuda_stream) {
+  if (!g) return TG_EINVAL;
+  const tv::GridImpl& G = g->impl;
+  if (!G.chan_mask) return TG_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (chan && cudaMemcpyAsync(chan, G.chan, (size_t)G.n * 16, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return TG_ECUDA;
+  if (vmaj && cudaMemcpyAsync(vmaj, G.vmaj, (size_t)G.n * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return TG_ECUDA;
+  return TG_OK;
+}
 
 extern "C" int leb_build(const float* density, const tg_volume_desc* vol, const tg_camera* cam,
                          float target_footprint_px, float variation_threshold, int32_t max_depth,

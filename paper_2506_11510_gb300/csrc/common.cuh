@@ -44,7 +44,8 @@ struct DevBuf {
     TV_CUDA(cudaMalloc(&p, count * sizeof(T)));
     n = count;
   }
-  void ensure(size_t count) { if (count > n) alloc(count); }
+  // grow geometrically: scratch that follows a growing size is reallocated O(log) times
+  void ensure(size_t count) { if (count > n) alloc(count > 2 * n ? count : 2 * n); }
   T* release() { T* r = p; p = nullptr; n = 0; return r; }
 };
 
@@ -82,6 +83,9 @@ struct GridImpl {
   int loc_R = 0;
   float* pool = nullptr;                 // scratch pool of the cached renderer (grown on demand)
   size_t pool_floats = 0;
+  float4* chan = nullptr;                // extra channels per cell: temperature, albedo, g, 0
+  float* vmaj = nullptr;                 // voxel majorant per cell
+  int chan_mask = 0;                     // 1 temperature, 2 albedo, 4 g, 8 majorants present
   ~GridImpl();
 };
 
@@ -109,10 +113,13 @@ __host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_
   return c;
 }
 
-// u in [0, 1): slot `slot` of path (pixel, sample); key (seed lo, seed hi ^ pixel),
-// counter (sample, slot / 4, 0, 0), 24 high bits of word slot % 4.
-__device__ __forceinline__ float rng_u(uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t slot) {
-  const uint4 o = philox10(make_uint4(sample, slot >> 2, 0u, 0u), (uint32_t)seed, (uint32_t)(seed >> 32) ^ pixel);
+// u in [0, 1): slot `slot` of stream `stream` of path (pixel, sample); key
+// (seed lo, seed hi ^ pixel), counter (sample, slot / 4, stream, 0), 24 high bits
+// of word slot % 4.  Stream 0 holds the fixed slots of a path (jitter, free paths,
+// phase); other streams hold draws whose number varies (delta tracking).
+__device__ __forceinline__ float rng_u(uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t slot,
+                                       uint32_t stream = 0u) {
+  const uint4 o = philox10(make_uint4(sample, slot >> 2, stream, 0u), (uint32_t)seed, (uint32_t)(seed >> 32) ^ pixel);
   const uint32_t s = slot & 3u;
   const uint32_t w = s == 0 ? o.x : s == 1 ? o.y : s == 2 ? o.z : o.w;
   return (float)(w >> 8) * 0x1p-24f;      // exact: 24-bit integer times a power of two

@@ -105,7 +105,20 @@ struct EstParams {
   int vtx_cap;                              // trace mode: training samples from the first vtx_cap collisions
   float* vtx;                               // [path][vtx_cap][8]: x (3), target, d (3), valid
   float ext[3];                             // domain extent in grid units (positions are stored over it)
+  // extended medium (EXT instantiations): extra per-cell channels, voxel medium
+  int ext_flags;                            // 1 emission, 2 per-cell albedo, 4 per-cell g, 8 voxel medium
+  float emission_scale;                     // emitted radiance per unit temperature
+  const float4* chan;                       // per cell: temperature, albedo, g, -
+  const float* vmaj;                        // per cell: voxel majorant
+  const float* voxel;                       // voxel densities [nz][ny][nx] of the voxel medium
+  int vdim[3];
+  float vn;                                 // voxels per grid unit (a power of two)
 };
+
+enum : int { EXT_EMISSION = 1, EXT_ALBEDO = 2, EXT_G = 4, EXT_VOXEL = 8 };
+// Random numbers of delta / ratio tracking: slot k (the k-th draw of the segment)
+// of stream 1 + 2b (free flight of bounce b) or 2 + 2b (its shadow ray), so that
+// ending one segment early never shifts the draws of another.
 
 // Pixel of the pix-th pixel in render order: TV_TILE x TV_TILE tiles, row-major
 // tiles, row-major inside a tile (when the tiles divide the image).
@@ -147,10 +160,17 @@ __device__ __forceinline__ bool box_intersect(const int C[3], float3 o, float3 d
   return tn < tf;
 }
 
-template <class Walker, int MODE>
+// EXT: the extended medium of the extra channels (Sec. 3): per-cell albedo and g,
+// emission (collision estimator, beta (1 - albedo) scale T at every real
+// collision), and the voxel medium -- the density at x is the voxel holding x --
+// tracked against the per-cell voxel majorants: delta tracking for free flights
+// (a tentative collision is real when u * majorant < rho(x), else the flight
+// goes on from x with a new free path), ratio tracking for shadow rays.
+template <class Walker, int MODE, bool EXT = false>
 __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const typename Walker::Params wp,
                                                                           const EstParams ep) {
   constexpr bool TRACE = MODE == MODE_TRACE;
+  const bool voxel = EXT && (ep.ext_flags & EXT_VOXEL);
   extern __shared__ double smem_d[];
   __shared__ float sun_inv[Walker::NDIR];
   Walker W(wp, smem_d);
@@ -178,6 +198,10 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
   int bounce = 0, seg_steps = 0, flags = 0, ncoll = 0, saved = 0, seqn = 0;
   int nv = 0;                                          // cache training vertices recorded
   bool queried = false;                                // the path ended into the cache
+  uint32_t nseg = 0;                                   // EXT: delta-tracking draws of the current segment
+  float gcur = M.g;                                    // EXT: phase parameter of the last collision
+  float Tr = 1.f;                                      // EXT: ratio-tracking transmittance
+  ff3 os = {ff_make(0.f), ff_make(0.f), ff_make(0.f)}; // EXT: shadow segment origin (voxel medium)
   long long psteps = 0;
   uint32_t c_paths = 0, c_steps = 0, c_shadow = 0, c_coll = 0, c_esc = 0, c_trunc = 0, c_lim = 0, c_miss = 0;
 
@@ -225,6 +249,21 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     }
     state = S_IDLE;
   };
+  auto draw = [&](uint32_t stream) { return rng_u(ep.seed, pixel, sample, nseg++, stream); };
+  // voxel medium: density of the voxel holding x (exact floor of the float-float coordinate)
+  auto voxel_at = [&](const ff3& x) -> float {
+    const ff xs[3] = {x.x, x.y, x.z};
+    int idx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float hs = xs[a].hi * ep.vn;
+      float fl = floorf(hs);
+      if (fl == hs && xs[a].lo < 0.f) fl -= 1.f;
+      int i = (int)fl;
+      idx[a] = i < 0 ? 0 : (i > ep.vdim[a] - 1 ? ep.vdim[a] - 1 : i);
+    }
+    return __ldg(ep.voxel + ((size_t)idx[2] * ep.vdim[1] + idx[1]) * ep.vdim[0] + idx[0]);
+  };
   // a free flight from o along d: SampleFreePath gives the optical depth to consume
   auto start_free = [&](int b) {
     float inv[Walker::NDIR];
@@ -234,6 +273,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     acc = ff_make(0.f);
     lim = -logf(1.0f - rng_u(ep.seed, pixel, sample, 2 + 3 * b));
     seg_steps = 0;
+    nseg = 0;
     mode = M_FREE;
     state = S_WALK;
   };
@@ -267,6 +307,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           sample = (uint32_t)s;
           flags = 0; ncoll = 0; psteps = 0; seqn = 0; L = ff_make(0.f); beta = 1.f; bounce = 0;
           nv = 0; queried = false;
+          if (EXT) gcur = M.g;
           const double u0 = rng_u(ep.seed, pixel, sample, 0), u1 = rng_u(ep.seed, pixel, sample, 1);
           const CamF& c = ep.cam;
           const double sx = (2.0 * (((double)px + u0) / (double)c.W) - 1.0) * c.tanF * c.aspect;
@@ -308,27 +349,81 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
         if (ev == EV_LIMIT) {
           // collision at parameter acc: albedo weight, then next-event estimation towards the sun
           o = ff3{ff_add(o.x, ff_mul(acc, d.x)), ff_add(o.y, ff_mul(acc, d.y)), ff_add(o.z, ff_mul(acc, d.z))};
-          beta *= M.albedo;
-          ++ncoll; ++c_coll;
-          record(-1);
-          saved = W.save();
-          W.begin(o, sun_inv);
-          t = 0.f;
-          acc = ff_make(0.f);
-          lim = TRACE ? INFINITY : SHADOW_TAU_CUTOFF;
-          seg_steps = 0;
-          mode = M_SHADOW;
-          state = S_WALK;
+          bool real = true;
+          if (voxel) {
+            // delta tracking: a tentative collision against the cell's voxel majorant
+            const float rx = voxel_at(o);
+            const float mj = __ldg(ep.vmaj + W.cell());
+            real = draw(1u + 2u * bounce) * mj < rx;
+            if (!real) {
+              // a null collision: fly on from o with a fresh free path, in the same cell
+              record(-1);
+              float inv[Walker::NDIR];
+              W.dir_table(d, inv);
+              W.begin(o, inv);
+              t = 0.f;
+              acc = ff_make(0.f);
+              lim = -logf(1.0f - draw(1u + 2u * bounce));
+              seg_steps = 0;
+              state = S_WALK;
+            }
+          }
+          if (real) {
+            if (EXT) {
+              const float4 ch = __ldg(ep.chan + W.cell());
+              const float alb = (ep.ext_flags & EXT_ALBEDO) ? ch.y : M.albedo;
+              if (ep.ext_flags & EXT_G) gcur = ch.z;
+              if (ep.ext_flags & EXT_EMISSION) L = ff_add(L, ff_make(beta * (1.0f - alb) * ep.emission_scale * ch.x));
+              beta *= alb;
+            } else {
+              beta *= M.albedo;
+            }
+            ++ncoll; ++c_coll;
+            record(-1);
+            saved = W.save();
+            W.begin(o, sun_inv);
+            t = 0.f;
+            acc = ff_make(0.f);
+            if (voxel) {
+              Tr = 1.f;
+              os = o;
+              nseg = 0;
+              lim = -logf(1.0f - draw(2u + 2u * bounce));
+            } else {
+              lim = TRACE ? INFINITY : SHADOW_TAU_CUTOFF;
+            }
+            seg_steps = 0;
+            mode = M_SHADOW;
+            state = S_WALK;
+          }
         } else {
           L = ff_add(L, ff_make(beta * M.Lenv)); ++c_esc;
           finish();
         }
+      } else if (voxel && ev == EV_LIMIT) {
+        // ratio tracking: a tentative collision on the shadow ray scales the transmittance
+        const ff3 w = {ff_make(M.sun_w[0]), ff_make(M.sun_w[1]), ff_make(M.sun_w[2])};
+        os = ff3{ff_add(os.x, ff_mul(acc, w.x)), ff_add(os.y, ff_mul(acc, w.y)), ff_add(os.z, ff_mul(acc, w.z))};
+        Tr *= 1.0f - voxel_at(os) / __ldg(ep.vmaj + W.cell());
+        if (!TRACE && Tr < 8.271806e-25f) {
+          // below 2^-80 the sun adds nothing visible: end the walk here (not in trace mode)
+          Tr = 0.f;
+          ev = EV_BOUNDARY;
+        } else {
+          W.begin(os, sun_inv);
+          t = 0.f;
+          acc = ff_make(0.f);
+          lim = -logf(1.0f - draw(2u + 2u * bounce));
+          seg_steps = 0;
+          state = S_WALK;
+        }
       } else {
         // the shadow walk ended: add the sun seen through it
         record(-1);
-        const float tr = ev == EV_BOUNDARY ? expf(-ff_float(acc)) : 0.0f;
+        const float tr = voxel ? Tr : (ev == EV_BOUNDARY ? expf(-ff_float(acc)) : 0.0f);
+        const float gg = EXT ? gcur : M.g;
         const float cs = d.x.hi * M.sun_w[0] + d.y.hi * M.sun_w[1] + d.z.hi * M.sun_w[2];
-        L = ff_add(L, ff_make(beta * hg_eval(M.g, cs) * M.E * tr));
+        L = ff_add(L, ff_make(beta * hg_eval(gg, cs) * M.E * tr));
         const float4 xq = make_float4(ff_float(o.x) / ep.ext[0], ff_float(o.y) / ep.ext[1],
                                       ff_float(o.z) / ep.ext[2], beta);
         if (TRACE && ep.vtx && nv < ep.vtx_cap) {
@@ -349,7 +444,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           finish();
         } else {
           // SamplePhaseFunction, then a new free flight from the collision point
-          const float3 nd = hg_scatter(M.g, rng_u(ep.seed, pixel, sample, 3 + 3 * bounce),
+          const float3 nd = hg_scatter(gg, rng_u(ep.seed, pixel, sample, 3 + 3 * bounce),
                                        rng_u(ep.seed, pixel, sample, 4 + 3 * bounce),
                                        make_float3(d.x.hi, d.y.hi, d.z.hi));
           d = ff3{ff_make(nd.x), ff_make(nd.y), ff_make(nd.z)};
@@ -370,13 +465,15 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       const Hop h = W.hop(t);
       if (!h.ok) { flags |= 16; finish(); break; }
       if (mode == M_FREE) ++c_steps; else ++c_shadow;
+      // the voxel medium walks the cells' majorants
+      const float rho = voxel ? __ldg(ep.vmaj + W.cell()) : h.rho;
       // optical depth of the cell: (sigma_unit * rho) * (t_exit - t), the product kept exactly
-      const ff sig = two_prod(M.sig_hi, h.rho);
+      const ff sig = two_prod(M.sig_hi, rho);
       const ff dtau = ff_mul_f(sig, h.texit - t);
       const ff sum = ff_add_fast(acc, dtau);
-      if (h.rho > 0.f && !ff_lt(sum, ff_make(lim))) {
+      if (rho > 0.f && !ff_lt(sum, ff_make(lim))) {
         // the segment's optical-depth limit falls inside this cell
-        if (mode == M_FREE) acc = ff_add(ff_make(t), ff_div(ff_sub(ff_make(lim), acc), sig));
+        if (mode == M_FREE || voxel) acc = ff_add(ff_make(t), ff_div(ff_sub(ff_make(lim), acc), sig));
         ev = EV_LIMIT;
         state = S_EVENT;
         break;
@@ -406,18 +503,18 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
 }
 
 // Launch the persistent estimator: as many resident blocks as fit, one wave.
-template <class Walker, int MODE>
+template <class Walker, int MODE, bool EXT = false>
 void launch_estimate(const typename Walker::Params& wp, const EstParams& ep, cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   TV_CUDA(cudaGetDevice(&dev));
   TV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const size_t shm = Walker::smem_bytes();
-  TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<Walker, MODE>, EST_BLOCK, shm));
+  TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<Walker, MODE, EXT>, EST_BLOCK, shm));
   if (per_sm < 1) per_sm = 1;
   long long blocks = (long long)sms * per_sm;
   const long long need = (ep.total + EST_BLOCK - 1) / EST_BLOCK;
   if (blocks > need) blocks = need < 1 ? 1 : need;
-  k_estimate<Walker, MODE><<<(unsigned)blocks, EST_BLOCK, shm, st>>>(wp, ep);
+  k_estimate<Walker, MODE, EXT><<<(unsigned)blocks, EST_BLOCK, shm, st>>>(wp, ep);
   TV_LAUNCH();
 }
 

@@ -10,7 +10,7 @@ GridImpl::~GridImpl() {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator, pool};
+  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator, pool, chan, vmaj};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (prev >= 0) cudaSetDevice(prev);

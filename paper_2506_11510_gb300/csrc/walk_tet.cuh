@@ -318,13 +318,13 @@ TetParams tet_params(const GridImpl& g);
 EstParams est_params(const GridImpl& g, const tg_camera& cam, const tg_medium& med, uint64_t seed);
 
 // The persistent estimator over a grid, instantiated for the grid's density format.
-template <int MODE>
+template <int MODE, bool EXT = false>
 void run_tet(const GridImpl& g, const EstParams& ep, cudaStream_t st) {
   const TetParams p = tet_params(g);
   switch (g.fmt) {
-    case TG_DENSITY_BF16: launch_estimate<TetWalker<TG_DENSITY_BF16>, MODE>(p, ep, st); break;
-    case TG_DENSITY_FP16: launch_estimate<TetWalker<TG_DENSITY_FP16>, MODE>(p, ep, st); break;
-    default: launch_estimate<TetWalker<TG_DENSITY_FP32>, MODE>(p, ep, st); break;
+    case TG_DENSITY_BF16: launch_estimate<TetWalker<TG_DENSITY_BF16>, MODE, EXT>(p, ep, st); break;
+    case TG_DENSITY_FP16: launch_estimate<TetWalker<TG_DENSITY_FP16>, MODE, EXT>(p, ep, st); break;
+    default: launch_estimate<TetWalker<TG_DENSITY_FP32>, MODE, EXT>(p, ep, st); break;
   }
 }
 
