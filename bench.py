@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--cpu-sample-px", type=int, default=0, help="side of the oracle's pixel window (0: auto)")
     p.add_argument("--no-cache", action="store_true", help="skip the radiance-cache time-to-equal-RMSE leg")
     p.add_argument("--no-ext", action="store_true", help="skip the extra-channel / voxel-medium frames")
+    p.add_argument("--no-rebuild", action="store_true", help="skip the moved-camera rebuild leg")
     p.add_argument("--cache-train-rounds", default="8,32,128", help="training budgets (rounds of 2^16 samples)")
     p.add_argument("--cache-ref-pixels", type=int, default=4096)
     p.add_argument("--cache-ref-spp", type=int, default=4096)
@@ -247,6 +248,9 @@ def run_ours(args):
     ext = None
     if not args.no_ext and rank == 0:
         ext = ext_leg(s, grid, vol, dev, comparator)
+    rebuild = None
+    if not args.no_rebuild and rank == 0:
+        rebuild = rebuild_leg(s, grid, vol)
 
     # end to end through the public API: host volume -> device, build, render, image -> host
     e2e = None
@@ -307,10 +311,46 @@ def run_ours(args):
                            "l2": "inputs larger than L2: grid records %.2f GB" % (ntets * 32 / 1e9),
                            "parallelism": "one frame per rank, disjoint sample ranges"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clk, "comparator": comparator, "cache": cache, "ext": ext}
+                "clocks": clk, "comparator": comparator, "cache": cache, "ext": ext, "rebuild": rebuild}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# rebuilds for a moved camera (animated camera)
+# ---------------------------------------------------------------------------
+def rebuild_leg(s, grid, vol):
+    """leb_rebuild from the frame's grid for cameras orbiting the target by a few
+    degrees (and a zoom), against a fresh leb_build for the same camera: time,
+    and whether the two grids are identical."""
+    import torch
+    import paper_2506_11510_gb300 as tv
+    from paper_2506_11510_gb300 import workloads as W
+    c = s.camera
+    tgt = c.target
+    res = []
+    for name, deg, zoom in (("orbit 1 deg", 1.0, 1.0), ("orbit 5 deg", 5.0, 1.0), ("zoom 10%", 0.0, 0.9)):
+        a = math.radians(deg)
+        vx, vz = c.pos[0] - tgt[0], c.pos[2] - tgt[2]
+        pos = (tgt[0] + zoom * (vx * math.cos(a) - vz * math.sin(a)), tgt[1] + zoom * (c.pos[1] - tgt[1]),
+               tgt[2] + zoom * (vx * math.sin(a) + vz * math.cos(a)))
+        s1 = W.with_camera(s, pos=pos)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        g1 = tv.rebuild_scene_grid(grid, s1, vol)
+        torch.cuda.synchronize()
+        t_re = (time.time() - t0) * 1e3
+        t0 = time.time()
+        g2 = tv.build_scene_grid(s1, vol)
+        torch.cuda.synchronize()
+        t_full = (time.time() - t0) * 1e3
+        same = g1.info.num_tets == g2.info.num_tets and all(
+            torch.equal(x, y) for x, y in zip(g1.export(("codes", "nbr")).values(), g2.export(("codes", "nbr")).values()))
+        res.append({"move": name, "tets": g1.info.num_tets, "rebuild_ms": round(t_re, 1),
+                    "fresh_build_ms": round(t_full, 1), "speedup": round(t_full / t_re, 3), "identical": bool(same)})
+        del g1, g2
+    return res
 
 
 # ---------------------------------------------------------------------------

@@ -102,6 +102,21 @@ int leb_build(const float* density, const tg_volume_desc* vol, const tg_camera* 
               float target_footprint_px, float variation_threshold, int32_t max_depth,
               int32_t density_format, void* cuda_stream, tg_grid** out);
 
+/*
+ * leb_rebuild - leb_build for a new camera (or footprint) on the same volume,
+ * reusing a previous grid of it: every node of the LEB tree that `prev` had
+ * (leaves and interior nodes, whose statistics a grid keeps) takes its
+ * statistics of D from there instead of scanning voxels; only nodes that `prev`
+ * never had are scanned.  The result is identical to leb_build with the same
+ * arguments.  Only `density` and the volume description must be those `prev`
+ * was built from (the statistics depend on nothing else; dims and K are
+ * checked, TG_EINVAL otherwise): camera, footprint, threshold and max_depth may
+ * all change.  `prev` must be a built grid (not imported) and stays valid.
+ */
+int leb_rebuild(const tg_grid* prev, const float* density, const tg_volume_desc* vol, const tg_camera* cam,
+                float target_footprint_px, float variation_threshold, int32_t max_depth, int32_t density_format,
+                void* cuda_stream, tg_grid** out);
+
 /* Size and shape of a grid.  Any output pointer may be NULL.  bytes: device bytes
  * the renderer reads (records + codes); K: vertex coordinate scale exponent. */
 int tg_grid_info(const tg_grid* g, int64_t* num_tets, int32_t* max_depth, int64_t* bytes,

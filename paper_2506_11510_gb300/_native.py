@@ -41,6 +41,8 @@ _VP, _I32, _I64, _U64, _F = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_fl
 SIGNATURES = {
     "leb_build": (C.c_int, [_VP, C.POINTER(TgVolumeDesc), C.POINTER(TgCamera), _F, _F, _I32, _I32, _VP,
                             C.POINTER(_VP)]),
+    "leb_rebuild": (C.c_int, [_VP, _VP, C.POINTER(TgVolumeDesc), C.POINTER(TgCamera), _F, _F, _I32, _I32, _VP,
+                              C.POINTER(_VP)]),
     "tg_grid_info": (C.c_int, [_VP, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64), C.POINTER(_I32),
                                C.POINTER(_I32)]),
     "tg_grid_export": (C.c_int, [_VP] + [_VP] * 12 + [_VP]),

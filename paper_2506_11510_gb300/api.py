@@ -160,6 +160,24 @@ def leb_build(density: torch.Tensor, box_min, voxel_size, camera=None, footprint
     return Grid(h, desc, density_format)
 
 
+def leb_rebuild(prev: Grid, density: torch.Tensor, box_min, voxel_size, camera=None, footprint_px: float = 0.0,
+                variation_threshold: float = -1.0, max_depth: int = 12, density_format: int = 0) -> Grid:
+    """leb_build for a new camera on the volume `prev` was built from, reusing its node statistics."""
+    _need(density, torch.float32, "density")
+    desc = volume_desc(density, box_min, voxel_size)
+    cam = C.byref(camera_struct(camera)) if camera is not None else None
+    h = C.c_void_p()
+    N.check(N.lib().leb_rebuild(prev.handle, _ptr(density), C.byref(desc), cam, float(footprint_px),
+                                float(variation_threshold), int(max_depth), int(density_format), _stream(),
+                                C.byref(h)), "leb_rebuild")
+    return Grid(h, desc, density_format)
+
+
+def rebuild_scene_grid(prev: Grid, scene, density: torch.Tensor) -> Grid:
+    return leb_rebuild(prev, density, scene.box_min, scene.voxel_size, scene.camera, scene.footprint_px,
+                       scene.variation_threshold, scene.max_depth, scene.density_format)
+
+
 def build_scene_grid(scene, density: torch.Tensor) -> Grid:
     return leb_build(density, scene.box_min, scene.voxel_size, scene.camera, scene.footprint_px,
                      scene.variation_threshold, scene.max_depth, scene.density_format)

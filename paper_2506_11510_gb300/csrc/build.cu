@@ -15,6 +15,7 @@
 // planes), then the criterion is evaluated once per new leaf.
 // Finalize: faces are matched through a hash of their vertex sums (verified
 // against the full vertex triples), then the 32-byte records are packed.
+#include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 #include <cuda_fp16.h>
 
@@ -57,6 +58,14 @@ struct LeafPtrs {
   uint32_t *cnt, *mn, *mx;
   unsigned long long* sum;
   uint8_t* crit;
+};
+
+// Statistics of the interior nodes of the LEB tree (each leaf that is split
+// leaves its code and statistics here), kept with the grid for rebuilds.
+struct NodePtrs {
+  unsigned long long* code;
+  unsigned long long* sum;
+  uint32_t *cnt, *mn, *mx;
 };
 
 struct Leaves {
@@ -464,6 +473,61 @@ __global__ void k_vmaj_store(LeafPtrs L, long long m, float* __restrict__ vmaj) 
   vmaj[i] = (float)(((double)L.mx[i] + 1.0) / 16777216.0);
 }
 
+// Rebuild: statistics of every node of a previous build of the same volume --
+// its leaves and its interior nodes, each sorted by code.
+struct PrevNodes {
+  const unsigned long long *leaf_code, *leaf_sum, *node_code, *node_sum;
+  const uint32_t *leaf_cnt, *leaf_mn, *leaf_mx, *node_cnt, *node_mn, *node_mx;
+  long long nleaf, nnode;
+};
+
+__device__ __forceinline__ long long find_code(const unsigned long long* a, long long n, unsigned long long c) {
+  long long lo = 0, hi = n;
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if (a[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return lo < n && a[lo] == c ? lo : -1;
+}
+
+// New leaves whose statistics a previous build already has take them from it;
+// the others are listed as misses (miss[j] = 1) for the voxel scan.
+__global__ void k_lookup(LeafPtrs L, const long long* list, long long m, PrevNodes P, uint8_t* known,
+                         unsigned long long* miss) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const long long i = list ? list[j] : j;
+  const unsigned long long c = L.code[i];
+  long long k = find_code(P.leaf_code, P.nleaf, c);
+  if (k >= 0) {
+    L.cnt[i] = P.leaf_cnt[k]; L.sum[i] = P.leaf_sum[k]; L.mn[i] = P.leaf_mn[k]; L.mx[i] = P.leaf_mx[k];
+  } else if ((k = find_code(P.node_code, P.nnode, c)) >= 0) {
+    L.cnt[i] = P.node_cnt[k]; L.sum[i] = P.node_sum[k]; L.mn[i] = P.node_mn[k]; L.mx[i] = P.node_mx[k];
+  }
+  known[j] = k >= 0 ? 1 : 0;
+  miss[j] = k >= 0 ? 0ull : 1ull;
+}
+
+__global__ void k_compact_misses(const long long* list, long long m, const unsigned long long* miss,
+                                 const unsigned long long* pos, long long* out) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m || !miss[j]) return;
+  out[pos[j]] = list ? list[j] : j;
+}
+
+// Interior-node statistics sorted by code (perm from the key sort)
+__global__ void k_iota(unsigned long long* a, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (unsigned long long)i;
+}
+
+__global__ void k_gather_nodes(NodePtrs src, const unsigned long long* perm, long long n, NodePtrs dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long k = (long long)perm[i];
+  dst.sum[i] = src.sum[k]; dst.cnt[i] = src.cnt[k]; dst.mn[i] = src.mn[k]; dst.mx[i] = src.mx[k];
+}
+
 // Sec. 2 criterion 2 in fp64 with every product and sum rounded on its own.
 __device__ bool camera_allows(const CamD& c, const Geo& g, const int x[4][3]) {
   if (!c.on) return true;
@@ -508,14 +572,14 @@ __device__ bool camera_allows(const CamD& c, const Geo& g, const int x[4][3]) {
 
 // A3 statistics, pass 3 (empty D -> voxel of the centroid) and the criterion of every new leaf
 __global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, const uint32_t* __restrict__ q,
-                               Crit C) {
+                               Crit C, const uint8_t* known) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   const long long i = list ? list[j] : j;
   int x[4][3];
   load_tet(L.v, i, x);
   const Geo& g = C.g;
-  small_leaf_stats<false>(L, i, x, q, g);
+  if (!known || !known[j]) small_leaf_stats<false>(L, i, x, q, g);
   if (L.cnt[i] == 0) {
     const int dims[3] = {g.nx, g.ny, g.nz};
     int idx[3];
@@ -565,7 +629,7 @@ __global__ void k_mark(LeafPtrs L, long long n, const unsigned long long* keys, 
 // A4: Maubach bisection of the marked leaves, copy of the others, stable order
 __global__ void k_split(LeafPtrs S, long long n, const unsigned long long* marks, const unsigned long long* pos,
                         LeafPtrs D, long long* newlist, unsigned long long* keys, unsigned long long mask,
-                        unsigned long long* vcount) {
+                        unsigned long long* vcount, NodePtrs arch, long long abase) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const long long before = (long long)pos[i];
@@ -575,6 +639,11 @@ __global__ void k_split(LeafPtrs S, long long n, const unsigned long long* marks
     D.code[j] = S.code[i]; D.tag[j] = S.tag[i]; D.crit[j] = S.crit[i];
     D.cnt[j] = S.cnt[i]; D.sum[j] = S.sum[i]; D.mn[j] = S.mn[i]; D.mx[j] = S.mx[i];
     return;
+  }
+  {
+    const long long a = abase + before;
+    arch.code[a] = S.code[i]; arch.sum[a] = S.sum[i];
+    arch.cnt[a] = S.cnt[i]; arch.mn[a] = S.mn[i]; arch.mx[a] = S.mx[i];
   }
   int x[4][3];
   load_tet(S.v, i, x);
@@ -732,26 +801,60 @@ struct Scanner {
 };
 
 // Statistics and criterion of m new leaves (list == nullptr: leaves 0..m-1).
+// Scratch of the rebuild's statistics lookup
+struct LookupBufs {
+  DevBuf<uint8_t> known;
+  DevBuf<unsigned long long> miss, pos;
+  DevBuf<long long> list;
+};
+
+// Statistics and criterion of m new leaves (list == nullptr: leaves 0..m-1).
+// With a previous build (prev), leaves it already had take its statistics and
+// only the others are scanned.
 void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const uint32_t* q, const Crit& C,
                          Scanner& scan, DevBuf<unsigned long long>& chunks, DevBuf<unsigned long long>& off,
-                         cudaStream_t st, int sms) {
+                         cudaStream_t st, int sms, const PrevNodes* prev, LookupBufs& lk) {
   if (m == 0) return;
   LeafPtrs L = Lv.ptrs();
-  chunks.ensure(m + 1);
-  off.ensure(m + 1);
-  k_stats_prep<false><<<blocks_for(m), TPB, 0, st>>>(L, list, m, C.g, chunks.p);
-  TV_LAUNCH();
-  TV_CUDA(cudaMemsetAsync(chunks.p + m, 0, sizeof(unsigned long long), st));
-  scan.exclusive(chunks.p, off.p, m + 1, st);
-  unsigned long long total = 0;
-  TV_CUDA(cudaMemcpyAsync(&total, off.p + m, sizeof total, cudaMemcpyDeviceToHost, st));
-  TV_CUDA(cudaStreamSynchronize(st));
-  if (total) {
-    const long long wblocks = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
-    k_stats_scan<false><<<(unsigned)wblocks, TPB, 0, st>>>(L, list, m, off.p, total, q, C.g);
+  const long long* slist = list;              // leaves to scan
+  long long sm = m;
+  const uint8_t* known = nullptr;
+  if (prev) {
+    lk.known.ensure(m);
+    lk.miss.ensure(m + 1);
+    lk.pos.ensure(m + 1);
+    lk.list.ensure(m);
+    k_lookup<<<blocks_for(m), TPB, 0, st>>>(L, list, m, *prev, lk.known.p, lk.miss.p);
     TV_LAUNCH();
+    TV_CUDA(cudaMemsetAsync(lk.miss.p + m, 0, sizeof(unsigned long long), st));
+    scan.exclusive(lk.miss.p, lk.pos.p, m + 1, st);
+    k_compact_misses<<<blocks_for(m), TPB, 0, st>>>(list, m, lk.miss.p, lk.pos.p, lk.list.p);
+    TV_LAUNCH();
+    unsigned long long nm = 0;
+    TV_CUDA(cudaMemcpyAsync(&nm, lk.pos.p + m, sizeof nm, cudaMemcpyDeviceToHost, st));
+    TV_CUDA(cudaStreamSynchronize(st));
+    slist = lk.list.p;
+    sm = (long long)nm;
+    known = lk.known.p;
   }
-  k_stats_finish<<<blocks_for(m), TPB, 0, st>>>(L, list, m, q, C);
+  if (sm > 0) {
+    chunks.ensure(sm + 1);
+    off.ensure(sm + 1);
+    k_stats_prep<false><<<blocks_for(sm), TPB, 0, st>>>(L, slist, sm, C.g, chunks.p);
+    TV_LAUNCH();
+    TV_CUDA(cudaMemsetAsync(chunks.p + sm, 0, sizeof(unsigned long long), st));
+    scan.exclusive(chunks.p, off.p, sm + 1, st);
+    unsigned long long total = 0;
+    TV_CUDA(cudaMemcpyAsync(&total, off.p + sm, sizeof total, cudaMemcpyDeviceToHost, st));
+    TV_CUDA(cudaStreamSynchronize(st));
+    if (total) {
+      const long long wblocks =
+          std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
+      k_stats_scan<false><<<(unsigned)wblocks, TPB, 0, st>>>(L, slist, sm, off.p, total, q, C.g);
+      TV_LAUNCH();
+    }
+  }
+  k_stats_finish<<<blocks_for(m), TPB, 0, st>>>(L, list, m, q, C, known);
   TV_LAUNCH();
 }
 
@@ -792,7 +895,7 @@ CamD camera_for_criterion(const tg_camera* cam, float footprint_px, const float 
 }  // namespace
 
 int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera* cam, float footprint_px,
-               float theta, int32_t max_depth, int32_t fmt, cudaStream_t st, GridImpl& G) {
+               float theta, int32_t max_depth, int32_t fmt, cudaStream_t st, GridImpl& G, const GridImpl* prev) {
   Geo g;
   g.nx = vol->nx; g.ny = vol->ny; g.nz = vol->nz;
   int n = 1, m = 0;
@@ -836,10 +939,29 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   k_insert_vertices<<<blocks_for(nroots), TPB, 0, st>>>(A.v.p, nroots, hkeys.p, hcap - 1, counters.p);
   TV_LAUNCH();
 
+  // a previous build of the same volume lends its node statistics
+  PrevNodes pn;
+  const PrevNodes* pp = nullptr;
+  if (prev) {
+    if (!prev->node_code || prev->K != g.K || prev->nvox[0] != g.nx || prev->nvox[1] != g.ny ||
+        prev->nvox[2] != g.nz)
+      return TG_EINVAL;
+    pn.leaf_code = prev->codes; pn.leaf_sum = prev->sum; pn.leaf_cnt = prev->count; pn.leaf_mn = prev->qmin;
+    pn.leaf_mx = prev->qmax; pn.nleaf = prev->n;
+    pn.node_code = prev->node_code; pn.node_sum = prev->node_sum; pn.node_cnt = prev->node_cnt;
+    pn.node_mn = prev->node_mn; pn.node_mx = prev->node_mx; pn.nnode = prev->n_nodes;
+    pp = &pn;
+  }
+  LookupBufs lk;
+
   Scanner scan;
   DevBuf<unsigned long long> chunks, off, marks, pos;
   DevBuf<long long> newlist;
-  stats_and_criterion(A, nullptr, nroots, q.p, C, scan, chunks, off, st, sms);
+  // interior nodes, appended as leaves are split
+  DevBuf<unsigned long long> acode, asum;
+  DevBuf<uint32_t> acnt, amn, amx;
+  long long nint = 0;
+  stats_and_criterion(A, nullptr, nroots, q.p, C, scan, chunks, off, st, sms, pp, lk);
 
   long long N = nroots;
   const int max_rounds = 4 * max_depth + 16;
@@ -874,13 +996,48 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     scan.exclusive(marks.p, pos.p, N + 1, st);
     B.ensure(N + M);
     newlist.ensure(2 * M);
+    if ((size_t)(nint + M) > acode.n) {
+      // grow the interior-node arrays (keep what they hold)
+      const size_t cap = std::max<size_t>(2 * (size_t)(nint + M), 1024);
+      DevBuf<unsigned long long> c2(cap), s2(cap);
+      DevBuf<uint32_t> n2(cap), m2(cap), x2(cap);
+      if (nint) {
+        TV_CUDA(cudaMemcpyAsync(c2.p, acode.p, nint * 8, cudaMemcpyDeviceToDevice, st));
+        TV_CUDA(cudaMemcpyAsync(s2.p, asum.p, nint * 8, cudaMemcpyDeviceToDevice, st));
+        TV_CUDA(cudaMemcpyAsync(n2.p, acnt.p, nint * 4, cudaMemcpyDeviceToDevice, st));
+        TV_CUDA(cudaMemcpyAsync(m2.p, amn.p, nint * 4, cudaMemcpyDeviceToDevice, st));
+        TV_CUDA(cudaMemcpyAsync(x2.p, amx.p, nint * 4, cudaMemcpyDeviceToDevice, st));
+        TV_CUDA(cudaStreamSynchronize(st));
+      }
+      acode = std::move(c2); asum = std::move(s2); acnt = std::move(n2); amn = std::move(m2); amx = std::move(x2);
+    }
+    const NodePtrs arch{acode.p, asum.p, acnt.p, amn.p, amx.p};
     k_split<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, marks.p, pos.p, B.ptrs(), newlist.p, hkeys.p, hcap - 1,
-                                           counters.p);
+                                           counters.p, arch, nint);
     TV_LAUNCH();
     std::swap(A, B);
     N += M;
-    stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, st, sms);
+    nint += M;
+    stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, st, sms, pp, lk);
   }
+
+  // ---- interior-node statistics sorted by code (for rebuilds) ----
+  DevBuf<unsigned long long> ncode(nint > 0 ? nint : 1), nsum(nint > 0 ? nint : 1);
+  DevBuf<uint32_t> ncnt(nint > 0 ? nint : 1), nmn(nint > 0 ? nint : 1), nmx(nint > 0 ? nint : 1);
+  if (nint > 0) {
+    DevBuf<unsigned long long> iota(nint), perm(nint);
+    k_iota<<<blocks_for(nint), TPB, 0, st>>>(iota.p, nint);
+    TV_LAUNCH();
+    size_t bytes = 0;
+    TV_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, acode.p, ncode.p, iota.p, perm.p, nint, 0, 64, st));
+    DevBuf<char> tmp(bytes + 16);
+    TV_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, bytes, acode.p, ncode.p, iota.p, perm.p, nint, 0, 64, st));
+    const NodePtrs src{acode.p, asum.p, acnt.p, amn.p, amx.p}, dst{ncode.p, nsum.p, ncnt.p, nmn.p, nmx.p};
+    k_gather_nodes<<<blocks_for(nint), TPB, 0, st>>>(src, perm.p, nint, dst);
+    TV_LAUNCH();
+    TV_CUDA(cudaStreamSynchronize(st));
+  }
+  acode.alloc(0); asum.alloc(0); acnt.alloc(0); amn.alloc(0); amx.alloc(0);
 
   // ---- finalize: neighbours, orientations, planes, densities, records ----
   const unsigned long long fcap = next_pow2(std::max<long long>(1024, 4 * N));
@@ -945,6 +1102,12 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   G.qmin = mn.release();
   G.qmax = mx.release();
   G.scratch = scratch.release();
+  G.n_nodes = nint;
+  G.node_code = ncode.release();
+  G.node_sum = nsum.release();
+  G.node_cnt = ncnt.release();
+  G.node_mn = nmn.release();
+  G.node_mx = nmx.release();
   build_locator(G, st);
   TV_CUDA(cudaStreamSynchronize(st));
   return TG_OK;
@@ -1061,7 +1224,34 @@ extern "C" int leb_build(const float* density, const tg_volume_desc* vol, const 
   int st;
   try {
     st = tv::build_grid(density, vol, cam, target_footprint_px, variation_threshold, max_depth, density_format,
-                        (cudaStream_t)cuda_stream, g->impl);
+                        (cudaStream_t)cuda_stream, g->impl, nullptr);
+  } catch (const tv::Error& e) {
+    st = e.code;
+  } catch (const std::bad_alloc&) {
+    st = TG_ENOMEM;
+  }
+  if (st != TG_OK) {
+    delete g;
+    return st;
+  }
+  *out = g;
+  return TG_OK;
+}
+
+extern "C" int leb_rebuild(const tg_grid* prev, const float* density, const tg_volume_desc* vol,
+                           const tg_camera* cam, float target_footprint_px, float variation_threshold,
+                           int32_t max_depth, int32_t density_format, void* cuda_stream, tg_grid** out) {
+  if (!prev || !density || !vol || !out || vol->nx <= 0 || vol->ny <= 0 || vol->nz <= 0 ||
+      !(vol->voxel_size > 0) || max_depth < 0 || max_depth > 50 || density_format < 0 || density_format > 2)
+    return TG_EINVAL;
+  if ((long long)vol->nx * vol->ny * vol->nz >= (1ll << 34)) return TG_EINVAL;
+  if (cam && !tv::camera_ok(cam)) return TG_EINVAL;
+  tg_grid* g = new (std::nothrow) tg_grid();
+  if (!g) return TG_ENOMEM;
+  int st;
+  try {
+    st = tv::build_grid(density, vol, cam, target_footprint_px, variation_threshold, max_depth, density_format,
+                        (cudaStream_t)cuda_stream, g->impl, &prev->impl);
   } catch (const tv::Error& e) {
     st = e.code;
   } catch (const std::bad_alloc&) {

@@ -86,6 +86,10 @@ struct GridImpl {
   float4* chan = nullptr;                // extra channels per cell: temperature, albedo, g, 0
   float* vmaj = nullptr;                 // voxel majorant per cell
   int chan_mask = 0;                     // 1 temperature, 2 albedo, 4 g, 8 majorants present
+  // statistics of the interior nodes of the LEB tree, sorted by code (rebuilds)
+  long long n_nodes = 0;
+  unsigned long long *node_code = nullptr, *node_sum = nullptr;
+  uint32_t *node_cnt = nullptr, *node_mn = nullptr, *node_mx = nullptr;
   ~GridImpl();
 };
 

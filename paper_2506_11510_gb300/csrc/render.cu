@@ -10,7 +10,8 @@ GridImpl::~GridImpl() {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator, pool, chan, vmaj};
+  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator, pool, chan, vmaj,
+                  node_code, node_sum, node_cnt, node_mn, node_mx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (prev >= 0) cudaSetDevice(prev);
