@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-cache", action="store_true", help="skip the radiance-cache time-to-equal-RMSE leg")
     p.add_argument("--no-ext", action="store_true", help="skip the extra-channel / voxel-medium frames")
     p.add_argument("--no-rebuild", action="store_true", help="skip the moved-camera rebuild leg")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched heterogeneous leg")
+    p.add_argument("--batch-jobs", type=int, default=64)
     p.add_argument("--cache-train-rounds", default="8,32,128", help="training budgets (rounds of 2^16 samples)")
     p.add_argument("--cache-ref-pixels", type=int, default=4096)
     p.add_argument("--cache-ref-spp", type=int, default=4096)
@@ -251,6 +253,9 @@ def run_ours(args):
     rebuild = None
     if not args.no_rebuild and rank == 0:
         rebuild = rebuild_leg(s, grid, vol)
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = batch_leg(args, dev)
 
     # end to end through the public API: host volume -> device, build, render, image -> host
     e2e = None
@@ -311,10 +316,84 @@ def run_ours(args):
                            "l2": "inputs larger than L2: grid records %.2f GB" % (ntets * 32 / 1e9),
                            "parallelism": "one frame per rank, disjoint sample ranges"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clk, "comparator": comparator, "cache": cache, "ext": ext, "rebuild": rebuild}
+                "clocks": clk, "comparator": comparator, "cache": cache, "ext": ext, "rebuild": rebuild,
+                "batch": batch}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched heterogeneous rendering
+# ---------------------------------------------------------------------------
+def batch_leg(args, dev):
+    """64 clouds of uneven size (64^3..384^3 voxels, 128^2..1024^2 views, 4..64 spp,
+    g in [-0.3, 0.8]) rendered by one persistent CUDA-graph launch (autotuned),
+    against the same jobs rendered one tet_render after another."""
+    import statistics as stt
+    import torch
+    import paper_2506_11510_gb300 as tv
+    from paper_2506_11510_gb300 import workloads as W
+    st = torch.cuda.current_stream()
+    scenes = W.batch_scenes(args.batch_jobs, seed=100)
+    jobs, tets = [], []
+    t0 = time.time()
+    for sc in scenes:
+        v = W.make_volume(sc, device=dev)
+        g = tv.build_scene_grid(sc, v)
+        del v
+        a = torch.zeros((sc.camera.height, sc.camera.width), dtype=torch.float32, device=dev)
+        jobs.append((g, sc.camera, sc.medium, sc.spp, sc.render_seed, a, None))
+        tets.append(g.info.num_tets)
+    torch.cuda.synchronize()
+    prep_s = time.time() - t0
+    paths = sum(sc.camera.width * sc.camera.height * sc.spp for sc in scenes)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # one job after another
+    for (g, cam, med, spp, seed, a, _) in jobs[:4]:
+        tv.tet_render(g, cam, med, spp, seed, 0, a, None, want_sq=False)
+    marks = [ev() for _ in range(len(jobs) + 1)]
+    marks[0].record(st)
+    for k, (g, cam, med, spp, seed, a, _) in enumerate(jobs):
+        tv.tet_render(g, cam, med, spp, seed, 0, a, None, want_sq=False)
+        marks[k + 1].record(st)
+    torch.cuda.synchronize()
+    seq_done = [marks[0].elapsed_time(m) for m in marks[1:]]
+    seq_ms = seq_done[-1]
+    # one launch
+    t0 = time.time()
+    b = tv.Batch(jobs, autotune=True)
+    torch.cuda.synchronize()
+    tune_s = time.time() - t0
+    b.render()
+    e0, e1 = ev(), ev()
+    reps = 3
+    e0.record(st)
+    for _ in range(reps):
+        b.render()
+    e1.record(st)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    knobs, job_ms = b.info()
+
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
+    res = {"jobs": len(jobs), "paths": paths, "tets_min": min(tets), "tets_max": max(tets),
+           "tets_median": int(stt.median(tets)), "setup_s": round(prep_s, 1),
+           "one_launch": {"ms": round(batch_ms, 2), "mpaths_s": round(paths / batch_ms / 1e3, 3),
+                          "job_latency_ms_p50": round(pct(job_ms, 0.5), 2),
+                          "job_latency_ms_p99": round(pct(job_ms, 0.99), 2), "knobs": knobs,
+                          "autotune_s": round(tune_s, 2), "graph": True},
+           "one_after_another": {"ms": round(seq_ms, 2), "mpaths_s": round(paths / seq_ms / 1e3, 3),
+                                 "job_latency_ms_p50": round(pct(seq_done, 0.5), 2),
+                                 "job_latency_ms_p99": round(pct(seq_done, 0.99), 2)},
+           "speedup": round(seq_ms / batch_ms, 3)}
+    b.free()
+    return res
 
 
 # ---------------------------------------------------------------------------

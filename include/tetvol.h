@@ -281,6 +281,47 @@ int tet_trace_ext_paths(const tg_grid* g, const tg_camera* cam, const tg_medium*
                         float* L, int32_t* flags, int32_t* collisions, int64_t* steps, void* cuda_stream);
 
 /* ==========================================================================
+ * Batched heterogeneous rendering: many grids (of one density format),
+ * cameras, media and images rendered by one persistent launch, captured in a
+ * CUDA graph.  Not in the paper: a property of the library.
+ * ========================================================================== */
+typedef struct {
+  const tg_grid* grid;
+  tg_camera cam;
+  tg_medium med;
+  int32_t spp;                /* >= 1 */
+  int32_t sample_offset;
+  uint64_t seed;
+  float* accum_sum;           /* device float[H][W], += */
+  float* accum_sumsq;         /* device float[H][W] or NULL, += */
+} tg_job;
+typedef struct tg_batch tg_batch;
+
+/*
+ * tg_batch_create - plan a batch of njobs (1..256) jobs.  Every path of every
+ * job is one work item of a single persistent launch: a warp lane's new path id
+ * selects its job, and the walker, camera, medium, random numbers (key: the
+ * job's seed and pixel, as tet_render) and image follow the job, so each image
+ * receives exactly what tet_render of its job would add.  With autotune != 0 the
+ * launch knobs -- idle lanes before a warp refills (4, 8, 16), waiting lanes
+ * before it handles events (8, 16, 24), resident blocks per SM (all, one less)
+ * and the job order (as given, or costliest first by paths x cells^(1/3)) -- are
+ * chosen on this batch by one pass of coordinate descent (each knob in turn
+ * takes the value whose timed launch, rendered into a scratch image, is
+ * fastest); otherwise 8, 16, all, as given.  The launch (counter resets
+ * and kernel) is then captured in a CUDA graph.  The grids and images must stay
+ * valid while the batch exists.  Synchronous.  TG_EINVAL for bad jobs or mixed
+ * density formats.
+ */
+int tg_batch_create(const tg_job* jobs, int32_t njobs, int32_t autotune, void* cuda_stream, tg_batch** out);
+/* tg_batch_render - one frame of every job: a single CUDA-graph launch on the stream. */
+int tg_batch_render(tg_batch* b, void* cuda_stream);
+/* tg_batch_info - knobs[4] = regen, events, blocks per SM (0 = all), order; job_ms[njobs] (host) = time
+ * from the first block's start to the end of each job's last path in the latest render (synchronous). */
+int tg_batch_info(const tg_batch* b, int32_t* knobs, double* job_ms);
+void tg_batch_free(tg_batch* b);
+
+/* ==========================================================================
  * Learned radiance cache.  A small MLP R(x, d) ends paths after one or two
  * collisions: it stands for the radiance that the rest of a path brings back,
  * is trained online on the tracer's own path vertices, and the plain tracer

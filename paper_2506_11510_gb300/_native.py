@@ -30,6 +30,12 @@ class TgVolumeDesc(C.Structure):
                 ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
 
 
+class TgJob(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("cam", TgCamera), ("med", TgMedium), ("spp", C.c_int32),
+                ("sample_offset", C.c_int32), ("seed", C.c_uint64), ("accum_sum", C.c_void_p),
+                ("accum_sumsq", C.c_void_p)]
+
+
 class TgExt(C.Structure):
     _fields_ = [("flags", C.c_int32), ("emission_scale", C.c_float), ("density", C.c_void_p)]
 
@@ -65,6 +71,10 @@ SIGNATURES = {
                                  _VP, _VP, _VP, _VP]),
     "tet_trace_ext_paths": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), C.POINTER(TgExt), _U64, _I64,
                                       _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "tg_batch_create": (C.c_int, [C.POINTER(TgJob), _I32, _I32, _VP, C.POINTER(_VP)]),
+    "tg_batch_render": (C.c_int, [_VP, _VP]),
+    "tg_batch_info": (C.c_int, [_VP, C.POINTER(_I32), C.POINTER(C.c_double)]),
+    "tg_batch_free": (None, [_VP]),
     "tg_random_paths": (C.c_int, [_U64, _I64, _I32, _I32, _I32, _VP, _VP, _VP, _VP]),
     "tet_cache_samples": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _U64, _I64, _VP, _VP, _VP, _I32,
                                     _VP, _VP, _VP]),

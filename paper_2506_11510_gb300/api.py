@@ -331,3 +331,52 @@ def tet_trace_ext_paths(grid: Grid, camera, medium, flags: int, seed: int, px, p
                                         _ptr(out["L"]), _ptr(out["flags"]), _ptr(out["collisions"]),
                                         _ptr(out["steps"]), _stream()), "tet_trace_ext_paths")
     return out
+
+
+class Batch:
+    """Many jobs (grid, camera, medium, spp, seed, image) rendered by one persistent
+    launch captured in a CUDA graph (tg_batch_*); render() adds one frame of every job."""
+
+    def __init__(self, jobs, autotune: bool = True):
+        """jobs: sequence of (grid, camera, medium, spp, seed, accum_sum, accum_sumsq or None[, sample_offset])."""
+        arr = (N.TgJob * len(jobs))()
+        self._keep = []
+        for k, j in enumerate(jobs):
+            grid, cam, med, spp, seed, s, s2 = j[:7]
+            off = j[7] if len(j) > 7 else 0
+            _need(s, torch.float32, "accum_sum", (cam.height, cam.width))
+            if s2 is not None:
+                _need(s2, torch.float32, "accum_sumsq", (cam.height, cam.width))
+            arr[k].grid = grid.handle.value
+            arr[k].cam = camera_struct(cam)
+            arr[k].med = medium_struct(med)
+            arr[k].spp = int(spp)
+            arr[k].sample_offset = int(off)
+            arr[k].seed = int(seed)
+            arr[k].accum_sum = s.data_ptr()
+            arr[k].accum_sumsq = s2.data_ptr() if s2 is not None else None
+            self._keep.append((grid, s, s2))
+        self._h = C.c_void_p()
+        self.n = len(jobs)
+        N.check(N.lib().tg_batch_create(arr, self.n, 1 if autotune else 0, _stream(), C.byref(self._h)),
+                "tg_batch_create")
+
+    def render(self):
+        N.check(N.lib().tg_batch_render(self._h, _stream()), "tg_batch_render")
+
+    def info(self):
+        knobs = (C.c_int32 * 4)()
+        ms = (C.c_double * self.n)()
+        N.check(N.lib().tg_batch_info(self._h, knobs, ms), "tg_batch_info")
+        return dict(zip(("regen_min", "ev_min", "blocks_per_sm", "order"), list(knobs))), list(ms)
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib().tg_batch_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -113,7 +113,34 @@ struct EstParams {
   const float* voxel;                       // voxel densities [nz][ny][nx] of the voxel medium
   int vdim[3];
   float vn;                                 // voxels per grid unit (a power of two)
+  // batch of grids (BATCH instantiations)
+  const void* jobs;                         // BatchJob<Walker::Params>[njobs]
+  int njobs;
+  unsigned long long* job_done;             // per job: paths finished
+  unsigned long long* job_time;             // per job: %globaltimer at its last path; [njobs]: first block's start
 };
+
+// One job of a batch (BATCH instantiations): a grid, a camera, a medium and an
+// image; paths [base, base + paths) of the launch are this job's.
+constexpr int BATCH_MAX_JOBS = 256;
+template <class WP>
+struct BatchJob {
+  WP wp;                                    // the job's grid (walker parameters)
+  CamF cam;
+  MedF med;
+  float sun_inv[32];                        // direction table of the job's sun
+  float* sum;
+  float* sumsq;
+  uint64_t seed;
+  long long base, paths;
+  int spp, sample_offset;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 enum : int { EXT_EMISSION = 1, EXT_ALBEDO = 2, EXT_G = 4, EXT_VOXEL = 8 };
 // Random numbers of delta / ratio tracking: slot k (the k-th draw of the segment)
@@ -166,16 +193,32 @@ __device__ __forceinline__ bool box_intersect(const int C[3], float3 o, float3 d
 // tracked against the per-cell voxel majorants: delta tracking for free flights
 // (a tentative collision is real when u * majorant < rho(x), else the flight
 // goes on from x with a new free path), ratio tracking for shadow rays.
-template <class Walker, int MODE, bool EXT = false>
+// BATCH: one launch over the paths of many jobs (BatchJob): a lane's new path
+// id selects its job (binary search over the jobs' first ids), and the walker,
+// camera, medium, seed and image follow the job.
+template <class Walker, int MODE, bool EXT = false, bool BATCH = false>
 __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const typename Walker::Params wp,
                                                                           const EstParams ep) {
   constexpr bool TRACE = MODE == MODE_TRACE;
   const bool voxel = EXT && (ep.ext_flags & EXT_VOXEL);
+  using Job = BatchJob<typename Walker::Params>;
+  const Job* jobs = static_cast<const Job*>(ep.jobs);
+  __shared__ long long job_base[BATCH ? BATCH_MAX_JOBS : 1];
+  const Job* job = nullptr;                            // BATCH: the lane's current job
+  float sig_l = 0.f;                                   // BATCH: its sigma per unit density (hi word)
   extern __shared__ double smem_d[];
   __shared__ float sun_inv[Walker::NDIR];
   Walker W(wp, smem_d);
-  const MedF& M = ep.med;
-  if (threadIdx.x == 0) {
+  auto med = [&]() -> const MedF& {
+    if constexpr (BATCH) return job->med;
+    else return ep.med;
+  };
+  const MedF& M0 = ep.med;
+  if (BATCH) {
+    for (int i = threadIdx.x; i < ep.njobs; i += blockDim.x) job_base[i] = jobs[i].base;
+    if (threadIdx.x == 0) atomicMin(ep.job_time + ep.njobs, global_ns());
+  } else if (threadIdx.x == 0) {
+    const MedF& M = M0;
     const ff3 w = {ff_make(M.sun_w[0]), ff_make(M.sun_w[1]), ff_make(M.sun_w[2])};
     float inv[Walker::NDIR];
     W.dir_table(w, inv);
@@ -199,7 +242,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
   int nv = 0;                                          // cache training vertices recorded
   bool queried = false;                                // the path ended into the cache
   uint32_t nseg = 0;                                   // EXT: delta-tracking draws of the current segment
-  float gcur = M.g;                                    // EXT: phase parameter of the last collision
+  float gcur = M0.g;                                   // EXT: phase parameter of the last collision
   float Tr = 1.f;                                      // EXT: ratio-tracking transmittance
   ff3 os = {ff_make(0.f), ff_make(0.f), ff_make(0.f)}; // EXT: shadow segment origin (voxel medium)
   long long psteps = 0;
@@ -239,8 +282,15 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       }
     }
     if (MODE == MODE_RENDER) {
-      atomicAdd(ep.sum + pixel, Lf);
-      if (ep.sumsq) atomicAdd(ep.sumsq + pixel, Lf * Lf);
+      float* sum = BATCH ? job->sum : ep.sum;
+      float* sumsq = BATCH ? job->sumsq : ep.sumsq;
+      atomicAdd(sum + pixel, Lf);
+      if (sumsq) atomicAdd(sumsq + pixel, Lf * Lf);
+      if (BATCH) {
+        const long long jb = job - jobs;
+        if (atomicAdd(ep.job_done + jb, 1ull) + 1ull == (unsigned long long)job->paths)
+          ep.job_time[jb] = global_ns();
+      }
     }
     if (MODE != MODE_RENDER && ep.cache_rec && !queried) {
       float4* r = reinterpret_cast<float4*>(ep.cache_rec) + 2 * pid;
@@ -249,7 +299,11 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     }
     state = S_IDLE;
   };
-  auto draw = [&](uint32_t stream) { return rng_u(ep.seed, pixel, sample, nseg++, stream); };
+  auto seedv = [&]() -> uint64_t {
+    if constexpr (BATCH) return job->seed;
+    else return ep.seed;
+  };
+  auto draw = [&](uint32_t stream) { return rng_u(seedv(), pixel, sample, nseg++, stream); };
   // voxel medium: density of the voxel holding x (exact floor of the float-float coordinate)
   auto voxel_at = [&](const ff3& x) -> float {
     const ff xs[3] = {x.x, x.y, x.z};
@@ -271,7 +325,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     W.begin(o, inv);
     t = 0.f;
     acc = ff_make(0.f);
-    lim = -logf(1.0f - rng_u(ep.seed, pixel, sample, 2 + 3 * b));
+    lim = -logf(1.0f - rng_u(seedv(), pixel, sample, 2 + 3 * b));
     seg_steps = 0;
     nseg = 0;
     mode = M_FREE;
@@ -299,17 +353,34 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           } else {
             // all samples of a pixel together; pixels tile by tile (row-major tiles), which keeps the
             // cells the warps in flight touch close together
-            const long long pix = pid / ep.spp;
-            s = ep.sample_offset + (int)(pid - pix * ep.spp);
-            render_pixel(pix, ep.cam.W, ep.cam.H, &px, &py);
+            long long local = pid;
+            int spp = ep.spp, soff = ep.sample_offset, cw = ep.cam.W, chh = ep.cam.H;
+            if constexpr (BATCH) {
+              // the job of this path: last job whose first path id <= pid
+              int lo = 0, hi = ep.njobs;
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (job_base[mid] <= pid) lo = mid + 1; else hi = mid;
+              }
+              job = jobs + (lo - 1);
+              W.set_job(&job->wp);
+              sig_l = job->med.sig_hi;
+              local = pid - job->base;
+              spp = job->spp; soff = job->sample_offset; cw = job->cam.W; chh = job->cam.H;
+            }
+            const long long pix = local / spp;
+            s = soff + (int)(local - pix * spp);
+            render_pixel(pix, cw, chh, &px, &py);
           }
-          pixel = (uint32_t)(py * ep.cam.W + px);
+          const int camW = BATCH ? job->cam.W : ep.cam.W;
+          pixel = (uint32_t)(py * camW + px);
           sample = (uint32_t)s;
           flags = 0; ncoll = 0; psteps = 0; seqn = 0; L = ff_make(0.f); beta = 1.f; bounce = 0;
           nv = 0; queried = false;
+          const MedF& M = med();
           if (EXT) gcur = M.g;
-          const double u0 = rng_u(ep.seed, pixel, sample, 0), u1 = rng_u(ep.seed, pixel, sample, 1);
-          const CamF& c = ep.cam;
+          const double u0 = rng_u(seedv(), pixel, sample, 0), u1 = rng_u(seedv(), pixel, sample, 1);
+          const CamF& c = BATCH ? job->cam : ep.cam;
           const double sx = (2.0 * (((double)px + u0) / (double)c.W) - 1.0) * c.tanF * c.aspect;
           const double sy = (2.0 * (((double)py + u1) / (double)c.H) - 1.0) * c.tanF;
           double dx = c.fwd[0] + sx * c.right[0] - sy * c.up[0];
@@ -345,6 +416,8 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     const unsigned pend = __ballot_sync(~0u, state == S_EVENT);
     const unsigned walking = __ballot_sync(~0u, state == S_WALK);
     if (pend && (walking == 0 || __popc(pend) >= ep.ev_min) && state == S_EVENT) {
+      const MedF& M = med();
+      const float* const sun_tab = BATCH ? job->sun_inv : sun_inv;
       if (mode == M_FREE) {
         if (ev == EV_LIMIT) {
           // collision at parameter acc: albedo weight, then next-event estimation towards the sun
@@ -381,7 +454,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
             ++ncoll; ++c_coll;
             record(-1);
             saved = W.save();
-            W.begin(o, sun_inv);
+            W.begin(o, sun_tab);
             t = 0.f;
             acc = ff_make(0.f);
             if (voxel) {
@@ -410,7 +483,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           Tr = 0.f;
           ev = EV_BOUNDARY;
         } else {
-          W.begin(os, sun_inv);
+          W.begin(os, sun_tab);
           t = 0.f;
           acc = ff_make(0.f);
           lim = -logf(1.0f - draw(2u + 2u * bounce));
@@ -444,8 +517,8 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           finish();
         } else {
           // SamplePhaseFunction, then a new free flight from the collision point
-          const float3 nd = hg_scatter(gg, rng_u(ep.seed, pixel, sample, 3 + 3 * bounce),
-                                       rng_u(ep.seed, pixel, sample, 4 + 3 * bounce),
+          const float3 nd = hg_scatter(gg, rng_u(seedv(), pixel, sample, 3 + 3 * bounce),
+                                       rng_u(seedv(), pixel, sample, 4 + 3 * bounce),
                                        make_float3(d.x.hi, d.y.hi, d.z.hi));
           d = ff3{ff_make(nd.x), ff_make(nd.y), ff_make(nd.z)};
           ++bounce;
@@ -468,7 +541,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       // the voxel medium walks the cells' majorants
       const float rho = voxel ? __ldg(ep.vmaj + W.cell()) : h.rho;
       // optical depth of the cell: (sigma_unit * rho) * (t_exit - t), the product kept exactly
-      const ff sig = two_prod(M.sig_hi, rho);
+      const ff sig = two_prod(BATCH ? sig_l : M0.sig_hi, rho);
       const ff dtau = ff_mul_f(sig, h.texit - t);
       const ff sum = ff_add_fast(acc, dtau);
       if (rho > 0.f && !ff_lt(sum, ff_make(lim))) {
@@ -503,18 +576,20 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
 }
 
 // Launch the persistent estimator: as many resident blocks as fit, one wave.
-template <class Walker, int MODE, bool EXT = false>
-void launch_estimate(const typename Walker::Params& wp, const EstParams& ep, cudaStream_t st) {
+template <class Walker, int MODE, bool EXT = false, bool BATCH = false>
+void launch_estimate(const typename Walker::Params& wp, const EstParams& ep, cudaStream_t st, int blocks_per_sm = 0) {
   int dev = 0, sms = 0, per_sm = 0;
   TV_CUDA(cudaGetDevice(&dev));
   TV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const size_t shm = Walker::smem_bytes();
-  TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<Walker, MODE, EXT>, EST_BLOCK, shm));
+  TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_estimate<Walker, MODE, EXT, BATCH>, EST_BLOCK,
+                                                       shm));
+  if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
   long long blocks = (long long)sms * per_sm;
   const long long need = (ep.total + EST_BLOCK - 1) / EST_BLOCK;
   if (blocks > need) blocks = need < 1 ? 1 : need;
-  k_estimate<Walker, MODE, EXT><<<(unsigned)blocks, EST_BLOCK, shm, st>>>(wp, ep);
+  k_estimate<Walker, MODE, EXT, BATCH><<<(unsigned)blocks, EST_BLOCK, shm, st>>>(wp, ep);
   TV_LAUNCH();
 }
 

@@ -157,11 +157,15 @@ __device__ __forceinline__ void tet_dir_table(const ff3& d, float invK, float in
 #define TV_PREFETCH 0                   // load the next cell's record as soon as the exit face is known
 #endif
 
-template <int FMT>
+// BATCH: the walker of a batch of grids -- the grid (and so its parameters)
+// changes from path to path and from lane to lane; set_job points it at one.
+template <int FMT, bool BATCH = false>
 struct TetWalker {
   using Params = TetParams;
   static constexpr int NDIR = TET_NID;      // direction-table entries
-  const TetParams& P;
+  const TetParams& P0;                      // the grid's parameters (uniform)
+  const TetParams* Pj = nullptr;            // BATCH: the current path's grid
+  const uint4* brec = nullptr;              // BATCH: its records
   double* tab;         // this thread's column: nO pair p at tab[p * EST_BLOCK] (9 slots), then the
                        // direction table as floats, entry q at ((float*)(tab0 + 9 EST_BLOCK))[q * EST_BLOCK]
   float* itab;
@@ -174,13 +178,26 @@ struct TetWalker {
   static size_t smem_bytes() { return (sizeof(double) * 9 + sizeof(float) * TET_NID) * EST_BLOCK; }
 
   __device__ TetWalker(const TetParams& p, double* smem)
-      : P(p), tab(smem + threadIdx.x), itab(reinterpret_cast<float*>(smem + 9 * EST_BLOCK) + threadIdx.x), cur(0),
+      : P0(p), tab(smem + threadIdx.x), itab(reinterpret_cast<float*>(smem + 9 * EST_BLOCK) + threadIdx.x), cur(0),
         nxt(0) {}
+
+  __device__ __forceinline__ const TetParams& prm() const {
+    if constexpr (BATCH) return *Pj;
+    else return P0;
+  }
+  __device__ __forceinline__ const uint4* recs() const {
+    if constexpr (BATCH) return brec;
+    else return P0.rec;
+  }
+  __device__ __forceinline__ void set_job(const TetParams* p) {
+    Pj = p;
+    brec = p->rec;
+  }
 
   __device__ __forceinline__ float2& pair(int q) { return *reinterpret_cast<float2*>(tab + q * EST_BLOCK); }
   __device__ __forceinline__ float2 pair(int q) const { return *reinterpret_cast<const float2*>(tab + q * EST_BLOCK); }
 
-  __device__ bool intersect(float3 o, float3 d, float* t_in) const { return box_intersect(P.C, o, d, t_in); }
+  __device__ bool intersect(float3 o, float3 d, float* t_in) const { return box_intersect(prm().C, o, d, t_in); }
 
   // Point location: start from the cell that holds the centre of p's locator-grid
   // cell and walk the straight segment from that centre to p; where the segment
@@ -188,6 +205,7 @@ struct TetWalker {
   // points) cells are coarse and this takes a step or two.  Falls back to the
   // exact descent of the LEB hierarchy.
   __device__ bool locate(float3 p) {
+    const TetParams& P = prm();
     long long c = -1;
     if (P.locator) {
       const float pc[3] = {p.x, p.y, p.z};
@@ -231,15 +249,16 @@ struct TetWalker {
     return c >= 0;
   }
 
-  __device__ __forceinline__ void dir_table(const ff3& d, float inv[TET_NID]) const { tet_dir_table(d, P.invK, inv); }
+  __device__ __forceinline__ void dir_table(const ff3& d, float inv[TET_NID]) const { tet_dir_table(d, prm().invK, inv); }
 
   // Per-segment table: nO[p] = (P[p] . o) 2^K as a float-float pair (so c - nO is
   // accurate to the distance walked, not to |o|), and the direction table.
   __device__ void begin(const ff3& o, const float* inv) {
     const ff no[9] = {o.x, o.y, o.z, ff_add(o.x, o.y), ff_sub(o.x, o.y), ff_add(o.y, o.z), ff_sub(o.y, o.z),
                       ff_add(o.x, o.z), ff_sub(o.x, o.z)};
+    const float scaleK = prm().scaleK;
 #pragma unroll
-    for (int p = 0; p < 9; ++p) pair(p) = make_float2(no[p].hi * P.scaleK, no[p].lo * P.scaleK);
+    for (int p = 0; p < 9; ++p) pair(p) = make_float2(no[p].hi * scaleK, no[p].lo * scaleK);
 #pragma unroll
     for (int q = 0; q < TET_NID; ++q) itab[q * EST_BLOCK] = inv[q];
   }
@@ -248,10 +267,10 @@ struct TetWalker {
 #if TV_LD256
     asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
-                 : "l"(P.rec + 2 * (size_t)cur));
+                 : "l"(recs() + 2 * (size_t)cur));
 #else
-    a = __ldg(P.rec + 2 * (size_t)cur);
-    b = __ldg(P.rec + 2 * (size_t)cur + 1);
+    a = __ldg(recs() + 2 * (size_t)cur);
+    b = __ldg(recs() + 2 * (size_t)cur + 1);
 #endif
   }
 
@@ -282,8 +301,8 @@ struct TetWalker {
     nxt = (int)(blink & NO_NBR);
 #if TV_PREFETCH
     if ((uint32_t)nxt != NO_NBR) {
-      na = __ldg(P.rec + 2 * (size_t)nxt);
-      nb = __ldg(P.rec + 2 * (size_t)nxt + 1);
+      na = __ldg(recs() + 2 * (size_t)nxt);
+      nb = __ldg(recs() + 2 * (size_t)nxt + 1);
     }
 #endif
     Hop h;

@@ -407,3 +407,29 @@ def make_channels(s: Scene, device="cpu", z_range: Optional[Tuple[int, int]] = N
         alb[a - z0:b - z0] = (qa.to(torch.float64) / ONE24).to(torch.float32)
         ani[a - z0:b - z0] = (qg.to(torch.float64) / ONE24).to(torch.float32)
     return temp, alb, ani
+
+
+def batch_scenes(n: int = 64, seed: int = 100, max_dim: int = 384):
+    """A heterogeneous batch: n cloud scenes (volume seeds seed..seed+n-1) with
+    cubic volumes of 64..max_dim voxels per edge, square views of 128..1024
+    pixels and 4..64 spp (each log-uniform), HG g uniform in [-0.3, 0.8],
+    albedo in [0.8, 0.95], up to 32 bounces, fp32 densities, adaptive grids
+    (1-pixel footprint, threshold 0.5)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dims = [d for d in (64, 96, 128, 192, 256, 384, 512) if d <= max_dim]
+    out = []
+    for k in range(n):
+        d = dims[int(rng.integers(0, len(dims)))]
+        res = int(round(2 ** rng.uniform(7, 10) / 16)) * 16
+        spp = int(round(2 ** rng.uniform(2, 6)))
+        g = float(rng.uniform(-0.3, 0.8))
+        alb = float(rng.uniform(0.8, 0.95))
+        depth = 3 * int(math.log2(d)) + 3
+        cam = Camera((0.5, 0.4, -1.2), (0.5, 0.5, 0.5), (0.0, 1.0, 0.0), 45.0, res, res)
+        med = Medium(alb, g, 64.0, 32, _norm((-1.0, -1.0, 1.0)), 3.0, 0.25)
+        out.append(Scene(name="batch%d" % k, dims=(d, d, d), recipe="cloud", volume_seed=seed + k,
+                         box_min=(0.0, 0.0, 0.0), voxel_size=1.0 / d, camera=cam, medium=med, spp=spp,
+                         render_seed=1000 + k, footprint_px=1.0, variation_threshold=0.5, max_depth=depth,
+                         density_format=0))
+    return out
