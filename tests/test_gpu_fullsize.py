@@ -179,3 +179,62 @@ def test_production_optical_depth_by_brute_force(production):
             t0 = torch.where(nd < 0, torch.maximum(t0, t), t0)
         tau = float((rho * torch.clamp(t1 - t0, min=0)).sum())
         assert got[r] == pytest.approx(tau, rel=1e-4, abs=1e-5)
+
+
+def test_production_cached_furnace_is_exact(production):
+    """Radiance cache at full size: in the white furnace a cache returning 1 makes
+    every path exactly 1, so every pixel of the cached frame sums to spp."""
+    from oracle import mlp as M
+    from paper_2506_11510_gb300 import cache as RC
+    s, _, grid = production
+    med = W.Medium(1.0, s.medium.g, s.medium.sigma_scale, 100000, s.medium.sun_dir, 0.0, 1.0)
+    p = torch.zeros(M.NUM_PARAMS, dtype=torch.float32, device="cuda")
+    p[M.O_B4] = 1.0
+    for depth in (1, 2):
+        img, _ = RC.render_cached(grid, s.camera, med, 2, 5, depth, p)
+        assert torch.all(img == 2.0)
+    assert RC.timeouts() == 0
+
+
+def test_production_channels_majorants_and_voxel_medium(production):
+    """Extra channels at full size: the voxel majorant bounds the voxel density at
+    points inside sampled cells, channel means lie in their ranges, and the
+    voxel-medium furnace (unit albedo channel) returns exactly 1 per path."""
+    import paper_2506_11510_gb300 as tv
+    s, vol, grid = production
+    t, a, g = W.make_channels(s, device="cuda")
+    grid.channels(vol, t, torch.ones_like(a), g)
+    chan, vmaj = grid.export_channels()
+    ex = grid.export(("verts",))
+    K = grid.info.K
+    n = s.dims[0] // 2                                    # voxels per cube edge (2 x 2 x 1 cubes)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    idx = torch.randint(0, vmaj.numel(), (200000,), device="cuda", generator=gen)
+    w = torch.distributions.Dirichlet(torch.ones(4, device="cuda")).sample((idx.numel(),))
+    w = 0.99 * w + 0.0025          # strictly inside: a point on a face may round to the far side of it
+    pts = (w[:, :, None] * ex["verts"][idx].double()).sum(1) * 2.0 ** (-K)
+    vi = torch.floor(pts * n).long()
+    vi[:, 0].clamp_(0, s.dims[0] - 1); vi[:, 1].clamp_(0, s.dims[1] - 1); vi[:, 2].clamp_(0, s.dims[2] - 1)
+    rho = vol[vi[:, 2], vi[:, 1], vi[:, 0]]
+    assert bool((rho <= vmaj[idx]).all())
+    assert float(chan[:, 0].min()) >= 0 and float(chan[:, 0].max()) <= 1
+    assert bool((chan[:, 1] == 1.0).all())
+    assert float(chan[:, 2].min()) >= -0.99 and float(chan[:, 2].max()) <= 0.99
+    med = W.Medium(0.3, s.medium.g, s.medium.sigma_scale, 100000, s.medium.sun_dir, 0.0, 1.0)
+    px, py, sm = W.random_path_ids(s, 20000, seed=6)
+    out = tv.tet_trace_ext_paths(grid, s.camera, med, 8 | 2 | 4, 3, px, py, sm, density=vol)
+    ok = (out["flags"].cpu().numpy() & 2) == 0
+    assert ok.mean() > 0.99 and np.all(out["L"].cpu().numpy()[ok] == 1.0)
+
+
+def test_production_rebuild_for_a_closer_camera(production):
+    """A camera moved close enough to change the grid: the rebuild equals the fresh build."""
+    import paper_2506_11510_gb300 as tv
+    s, vol, grid = production
+    s1 = W.with_camera(s, pos=(1.0, 1.0, -0.6))
+    g1 = tv.rebuild_scene_grid(grid, s1, vol)
+    g2 = tv.build_scene_grid(s1, vol)
+    assert g1.info.num_tets == g2.info.num_tets
+    e1, e2 = g1.export(("codes", "nbr", "density")), g2.export(("codes", "nbr", "density"))
+    for k in e1:
+        assert torch.equal(e1[k], e2[k]), k
