@@ -312,6 +312,7 @@ def run_ours(args):
                            "tets": ntets, "grid_depth": grid_depth, "build_ms": round(build_ms, 1),
                            "width": W_, "height": H_, "spp": spp, "paths_per_frame": int(paths),
                            "tet_steps_per_path": round(steps_per_frame / paths, 2),
+                           "g_tet_steps_per_s": round(steps_per_frame / (mean_launch_ms * 1e-3) / 1e9, 3),
                            "collisions_per_path": round(counters["collisions"] / paths, 3),
                            "density_storage": {0: "fp32", 1: "bf16", 2: "fp16"}[s.density_format],
                            "l2": "inputs larger than L2: grid records %.2f GB" % (ntets * 32 / 1e9),
@@ -596,13 +597,15 @@ def oracle_window_render(s, g, wcam, min_seconds=10.0, nthreads=0):
     py, px, sm = np.meshgrid(np.arange(side), np.arange(side), np.arange(s.spp), indexing="ij")
     px, py, sm = px.ravel(), py.ravel(), sm.ravel()
     t0 = time.time()
-    paths, k = 0, 0
+    paths, k, steps = 0, 0, 0
     while k < 256:
-        g.render_paths(wcam, s.medium, s.render_seed, px, py, sm + k * s.spp, nthreads=nthreads)
+        r = g.render_paths(wcam, s.medium, s.render_seed, px, py, sm + k * s.spp, nthreads=nthreads)
         paths += len(px)
+        steps += int(r["steps"].sum())
         k += 1
         if time.time() - t0 >= min_seconds:
             break
+    oracle_window_render.steps = steps
     return paths, time.time() - t0
 
 
@@ -619,8 +622,10 @@ def cpu_baseline(args, s, vol):
     side = args.cpu_sample_px or 64
     g, wcam, tb = oracle_window(s, vol_np, side)
     paths, tr = oracle_window_render(s, g, wcam)
+    steps = oracle_window_render.steps
     return {"value": round(paths / tr / 1e6, 5), "unit": "Mpaths/s", "cores": cores, "kind": "oracle",
-            "sample": cpu_sample_text(side, s, paths, tb), "render_s": round(tr, 2)}
+            "sample": cpu_sample_text(side, s, paths, tb), "render_s": round(tr, 2),
+            "tet_steps_per_path": round(steps / paths, 1), "g_tet_steps_per_s": round(steps / tr / 1e9, 4)}
 
 
 def run_reference(args):
@@ -639,11 +644,12 @@ def run_reference(args):
     g, wcam, tb = oracle_window(s, vol, side)
     for _ in range(args.warmup):
         oracle_window_render(s, g, wcam, min_seconds=0.0)
-    times, counts = [], []
+    times, counts, nsteps = [], [], 0
     for _ in range(max(1, args.steps)):
         paths, tr = oracle_window_render(s, g, wcam, min_seconds=5.0)
         times.append(tr)
         counts.append(paths)
+        nsteps += oracle_window_render.steps
     mean = sum(times) / len(times)
     value = sum(counts) / sum(times) / 1e6
     cores = os.cpu_count() or 1
@@ -655,7 +661,9 @@ def run_reference(args):
                        "ms_per_frame_extrapolated": round(s.camera.width * s.camera.height * s.spp / value / 1e3, 1),
                        "sample": "the CPU oracle on a %dx%d-pixel window of the frame" % (side, side)},
             "cpu_baseline": {"value": round(value, 5), "unit": "Mpaths/s", "cores": cores, "kind": "oracle",
-                             "sample": cpu_sample_text(side, s, paths, tb)},
+                             "sample": cpu_sample_text(side, s, paths, tb),
+                             "tet_steps_per_path": round(nsteps / sum(counts), 1),
+                             "g_tet_steps_per_s": round(nsteps / sum(times) / 1e9, 4)},
             "e2e": {"value": round(value, 5), "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
