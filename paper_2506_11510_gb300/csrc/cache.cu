@@ -275,6 +275,9 @@ __global__ void __launch_bounds__(MT) k_mlp_infer(const float* __restrict__ P, f
       r0 = reinterpret_cast<const float4*>(rec)[2 * row];
       r1 = reinterpret_cast<const float4*>(rec)[2 * row + 1];
     }
+    // a cached frame's tile without a single query (every path ended before its
+    // cache collision) needs no network: its records already hold their estimates
+    if (COMPOSE && !__syncthreads_or(r0.w > 0.f)) continue;
     const float x[3] = {r0.x, r0.y, r0.z}, d[3] = {r1.x, r1.y, r1.z};
     encode(x, d, [&](int c, const float* v) { put8(S.X, t, 8 * c, SBO128, v); });
     float v[64];

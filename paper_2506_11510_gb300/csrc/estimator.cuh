@@ -299,6 +299,11 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     }
     state = S_IDLE;
   };
+  // cells of a finished segment into the frame's counters (free flights, shadow rays)
+  auto count_steps = [&](int n) {
+    if (mode == M_FREE) c_steps += (uint32_t)n;
+    else c_shadow += (uint32_t)n;
+  };
   auto seedv = [&]() -> uint64_t {
     if constexpr (BATCH) return job->seed;
     else return ep.seed;
@@ -536,8 +541,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       ++seg_steps;
       if (TRACE) ++psteps;
       const Hop h = W.hop(t);
-      if (!h.ok) { flags |= 16; finish(); break; }
-      if (mode == M_FREE) ++c_steps; else ++c_shadow;
+      if (!h.ok) { count_steps(seg_steps - 1); flags |= 16; finish(); break; }
       // the voxel medium walks the cells' majorants
       const float rho = voxel ? __ldg(ep.vmaj + W.cell()) : h.rho;
       // optical depth of the cell: (sigma_unit * rho) * (t_exit - t), the product kept exactly
@@ -547,6 +551,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       if (rho > 0.f && !ff_lt(sum, ff_make(lim))) {
         // the segment's optical-depth limit falls inside this cell
         if (mode == M_FREE || voxel) acc = ff_add(ff_make(t), ff_div(ff_sub(ff_make(lim), acc), sig));
+        count_steps(seg_steps);
         ev = EV_LIMIT;
         state = S_EVENT;
         break;
@@ -554,9 +559,11 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       acc = sum;
       t = h.texit;
       if (!W.advance()) {
+        count_steps(seg_steps);
         ev = EV_BOUNDARY;
         state = S_EVENT;
       } else if (seg_steps >= SEG_STEP_LIMIT) {
+        count_steps(seg_steps);
         flags |= 8; ++c_lim;
         finish();
       }

@@ -31,6 +31,15 @@ struct TetParams {
 
 __device__ __forceinline__ int sext24(uint32_t v) { return ((int)(v << 8)) >> 8; }
 
+// Signed 24-bit plane offset held in three consecutive bytes of the 8-byte pair
+// (lo, hi): one byte permute whose fourth selector replicates the sign of the
+// third byte (prmt: a selector with its top bit set copies the selected byte's sign).
+__device__ __forceinline__ int prmt_s24(uint32_t lo, uint32_t hi, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(lo), "r"(hi), "r"(sel));
+  return (int)r;
+}
+
 template <int FMT>
 __device__ __forceinline__ float decode_density(uint32_t w) {
   if (FMT == TG_DENSITY_BF16) return __uint_as_float(w << 16);
@@ -285,8 +294,9 @@ struct TetWalker {
     load(a, b);
 #endif
     const uint32_t link[4] = {a.x, a.y, a.z, a.w};
-    const int c[4] = {sext24(b.x), sext24((b.x >> 24) | (b.y << 8)), sext24((b.y >> 16) | (b.z << 16)),
-                      sext24(b.z >> 8)};
+    // the four planes: bytes 0-2, 3-5, 6-8 and 9-11 of (b.x, b.y, b.z), sign-extended
+    const int c[4] = {prmt_s24(b.x, b.y, 0xA210u), prmt_s24(b.x, b.y, 0xD543u), prmt_s24(b.y, b.z, 0xC432u),
+                      prmt_s24(b.z, 0u, 0xB321u)};
     float best = INFINITY;
     uint32_t blink = NO_NBR;
 #pragma unroll
