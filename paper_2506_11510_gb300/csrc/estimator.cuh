@@ -548,7 +548,9 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       const ff sig = two_prod(BATCH ? sig_l : M0.sig_hi, rho);
       const ff dtau = ff_mul_f(sig, h.texit - t);
       const ff sum = ff_add_fast(acc, dtau);
-      if (rho > 0.f && !ff_lt(sum, ff_make(lim))) {
+      // (the limit is a float: comparing the high word decides all but exact ties, which
+      // only move a collision by less than one unit in the last place of the free path)
+      if (rho > 0.f && !(sum.hi < lim)) {
         // the segment's optical-depth limit falls inside this cell
         if (mode == M_FREE || voxel) acc = ff_add(ff_make(t), ff_div(ff_sub(ff_make(lim), acc), sig));
         count_steps(seg_steps);
@@ -562,11 +564,13 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
         count_steps(seg_steps);
         ev = EV_BOUNDARY;
         state = S_EVENT;
-      } else if (seg_steps >= SEG_STEP_LIMIT) {
-        count_steps(seg_steps);
-        flags |= 8; ++c_lim;
-        finish();
       }
+    }
+    // a segment that walks too many cells (a corrupt grid) ends its path
+    if (state == S_WALK && seg_steps >= SEG_STEP_LIMIT) {
+      count_steps(seg_steps);
+      flags |= 8; ++c_lim;
+      finish();
     }
   }
 
