@@ -304,11 +304,11 @@ typedef struct tg_batch tg_batch;
  * job's seed and pixel, as tet_render) and image follow the job, so each image
  * receives exactly what tet_render of its job would add.  With autotune != 0 the
  * launch knobs -- idle lanes before a warp refills (4, 8, 16), waiting lanes
- * before it handles events (8, 16, 24), resident blocks per SM (all, one less)
+ * before it handles events (8, 12, 16), resident blocks per SM (all, one less)
  * and the job order (as given, or costliest first by paths x cells^(1/3)) -- are
  * chosen on this batch by one pass of coordinate descent (each knob in turn
  * takes the value whose timed launch, rendered into a scratch image, is
- * fastest); otherwise 8, 16, all, as given.  The launch (counter resets
+ * fastest); otherwise 8, 12, all, as given.  The launch (counter resets
  * and kernel) is then captured in a CUDA graph.  The grids and images must stay
  * valid while the batch exists.  Synchronous.  TG_EINVAL for bad jobs or mixed
  * density formats.

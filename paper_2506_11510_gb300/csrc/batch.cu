@@ -37,7 +37,7 @@ struct tg_batch {
   tv::DevBuf<tv::Job> table;
   tv::DevBuf<unsigned long long> done, times;
   tv::DevBuf<float> scratch;                     // tuning renders go here
-  tv::Knobs knobs{8, 16, 0, 0};
+  tv::Knobs knobs{TV_REGEN_MIN, TV_EV_MIN, 0, 0};
   long long total = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -201,7 +201,7 @@ int tg_batch_create(const tg_job* jobs, int32_t njobs, int32_t autotune, void* c
       for (int knob = 0; knob < 4; ++knob) {
         std::vector<int> values;
         if (knob == 0) values = {4, 8, 16};
-        else if (knob == 1) values = {8, 16, 24};
+        else if (knob == 1) values = {8, 12, 16};
         else if (knob == 2) values = {0, bps_alt};
         else values = {0, 1};
         for (int v : values) {

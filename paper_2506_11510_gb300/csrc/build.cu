@@ -718,7 +718,7 @@ __device__ __forceinline__ uint32_t encode_density(double mean, int fmt) {
   const float f = __double2float_rn(mean);
   if (fmt == TG_DENSITY_BF16) {
     const uint32_t u = __float_as_uint(f);
-    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+    return ((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16) << 16;   // the high half: the word reads as the float
   }
   if (fmt == TG_DENSITY_FP16) return (uint32_t)__half_as_ushort(__float2half_rn(f));
   return __float_as_uint(f);

@@ -56,7 +56,8 @@ struct DevBuf {
 //                       p | s << 4 (outward normal (-1)^s P[p])
 //   word 4..6  the four plane offsets P[p] . v in units of 2^-K cube, as
 //              24-bit two's complement integers packed back to back
-//   word 7     density: fp32 bits, or bf16 / fp16 bits in the low half
+//   word 7     density: fp32 bits; bf16 bits in the high half with the low half
+//              zero (the word is the density as a float); or fp16 bits in the low half
 // ---------------------------------------------------------------------------
 constexpr uint32_t NO_NBR = 0x7FFFFFFu;
 constexpr int64_t MAX_TETS = 0x7FFFFFE;

@@ -52,13 +52,13 @@ constexpr int EST_BLOCK = 256;
 #define TV_REGEN_MIN 8                  // idle lanes before a warp fetches new paths
 #endif
 #ifndef TV_EV_MIN
-#define TV_EV_MIN 16                    // waiting lanes before a warp handles events
+#define TV_EV_MIN 12                    // waiting lanes before a warp handles events
 #endif
 #ifndef TV_TILE
 #define TV_TILE 64                      // pixels are handed out in TV_TILE x TV_TILE tiles (when they divide the image)
 #endif
 #ifndef TV_STEPS_PER_ROUND
-#define TV_STEPS_PER_ROUND 8            // cell steps between two warp-wide regeneration / event rounds
+#define TV_STEPS_PER_ROUND 16           // cell steps between two warp-wide regeneration / event rounds
 #endif
 constexpr int SEG_STEP_LIMIT = 1 << 20;      // cells per segment before a walk gives up
 // A shadow walk whose optical depth passes this value contributes at most

@@ -54,7 +54,7 @@ __global__ void k_import(uint4* __restrict__ rec, long long n, int K, int fmt, c
   const float r = density[i];
   if (fmt == TG_DENSITY_BF16) {
     const uint32_t u = __float_as_uint(r);
-    w = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+    w = ((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16) << 16;
   } else if (fmt == TG_DENSITY_FP16) {
     w = (uint32_t)__half_as_ushort(__float2half_rn(r));
   } else {

@@ -42,7 +42,7 @@ __device__ __forceinline__ int prmt_s24(uint32_t lo, uint32_t hi, uint32_t sel) 
 
 template <int FMT>
 __device__ __forceinline__ float decode_density(uint32_t w) {
-  if (FMT == TG_DENSITY_BF16) return __uint_as_float(w << 16);
+  if (FMT == TG_DENSITY_BF16) return __uint_as_float(w);          // bf16 in the high half, low half zero
   if (FMT == TG_DENSITY_FP16) return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
   return __uint_as_float(w);
 }
