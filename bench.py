@@ -147,11 +147,13 @@ def profiled_traffic(scene_name):
 def workload_name(s):
     """The workload, named by the scene's recipe and sizes (the same for both arms)."""
     nx, ny, nz = s.dims
-    return ("%s: %dx%dx%d procedural cloud, adaptive LEB grid (%s density), %dx%d @ %d spp, "
-            "albedo %.2f, g %.1f, <= %d bounces" % (s.name, nx, ny, nz,
-                                                     {0: "FP32", 1: "BF16", 2: "FP16"}[s.density_format],
-                                                     s.camera.width, s.camera.height, s.spp, s.medium.albedo,
-                                                     s.medium.g, s.medium.max_bounces))
+    vol = {"sphere": "fBm-perturbed sphere", "cloud": "fBm cloud", "wispy": "fBm x Worley cloud"}.get(s.recipe,
+                                                                                                  s.recipe)
+    uniform = s.variation_threshold < 0 and s.footprint_px <= 0
+    grid = ("uniform LEB grid, depth %d" % s.max_depth) if uniform else "adaptive LEB grid"
+    return ("%s: %dx%dx%d %s, %s (%s density), %dx%d @ %d spp, albedo %.2f, g %.1f, <= %d bounces"
+            % (s.name, nx, ny, nz, vol, grid, {0: "FP32", 1: "BF16", 2: "FP16"}[s.density_format],
+               s.camera.width, s.camera.height, s.spp, s.medium.albedo, s.medium.g, s.medium.max_bounces))
 
 
 # ---------------------------------------------------------------------------
