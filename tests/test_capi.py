@@ -84,3 +84,36 @@ def test_radiance_cache_argument_checks_need_no_gpu():
     assert L.tg_random_paths(0, 4, 8, 8, (1 << 31) - 2, fake, fake, fake, None) == N.TG_EINVAL
     assert L.rc_mlp_grad(fake, fake, 0, fake, fake, None) == N.TG_OK                              # nothing to do
     assert N.RC_NUM_PARAMS == 64 * 128 + 64 + 2 * (64 * 64 + 64) + 64 + 1
+
+
+def test_rebuild_batch_and_channel_argument_checks_need_no_gpu():
+    import ctypes as C
+    from paper_2506_11510_gb300 import _native as N
+    L = N.lib()
+    desc = N.TgVolumeDesc()
+    desc.nx = desc.ny = desc.nz = 8
+    desc.voxel_size = 0.125
+    out = C.c_void_p()
+    fake = C.c_void_p(256)
+    assert L.leb_rebuild(None, fake, C.byref(desc), None, 0.0, -1.0, 4, 0, None, C.byref(out)) == N.TG_EINVAL
+    assert L.leb_rebuild(fake, None, C.byref(desc), None, 0.0, -1.0, 4, 0, None, C.byref(out)) == N.TG_EINVAL
+    assert L.leb_rebuild(fake, fake, C.byref(desc), None, 0.0, -1.0, 51, 0, None, C.byref(out)) == N.TG_EINVAL
+    assert L.tg_batch_create(None, 1, 0, None, C.byref(out)) == N.TG_EINVAL
+    jobs = (N.TgJob * 1)()
+    assert L.tg_batch_create(jobs, 0, 0, None, C.byref(out)) == N.TG_EINVAL          # no jobs
+    assert L.tg_batch_create(jobs, 257, 0, None, C.byref(out)) == N.TG_EINVAL        # too many
+    assert L.tg_batch_create(jobs, 1, 0, None, C.byref(out)) == N.TG_EINVAL          # NULL grid
+    assert L.tg_batch_render(None, None) == N.TG_EINVAL
+    assert L.tg_batch_info(None, None, None) == N.TG_EINVAL
+    assert L.tg_grid_channels(None, fake, None, None, None, None) == N.TG_EINVAL
+    assert L.tg_grid_channels(fake, None, None, None, None, None) == N.TG_EINVAL
+    assert L.tg_grid_export_channels(None, None, None, None) == N.TG_EINVAL
+    cam, med = N.TgCamera(), N.TgMedium()
+    cam.width = cam.height = 8
+    cam.fov_y_deg = 40.0
+    med.max_bounces = 4
+    ext = N.TgExt()
+    assert L.tet_render_ext(None, C.byref(cam), C.byref(med), C.byref(ext), 1, 0, 0, fake, None, None,
+                            None) == N.TG_EINVAL
+    assert L.tet_trace_ext_paths(None, C.byref(cam), C.byref(med), C.byref(ext), 0, 1, fake, fake, fake, None,
+                                 None, None, None, None) == N.TG_EINVAL
