@@ -188,7 +188,11 @@ struct TetWalker {
 
   __device__ TetWalker(const TetParams& p, double* smem)
       : P0(p), tab(smem + threadIdx.x), itab(reinterpret_cast<float*>(smem + 9 * EST_BLOCK) + threadIdx.x), cur(0),
-        nxt(0) {}
+        nxt(0) {
+#if TV_PREFETCH
+    ra = rb = na = nb = make_uint4(NO_NBR, NO_NBR, NO_NBR, NO_NBR);
+#endif
+  }
 
   __device__ __forceinline__ const TetParams& prm() const {
     if constexpr (BATCH) return *Pj;
@@ -234,6 +238,9 @@ struct TetWalker {
         const float len = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
         cur = start;
         c = start;
+#if TV_PREFETCH
+        load(ra, rb);        // the walk below reads the current cell's record from ra, rb
+#endif
         if (len > 0.f) {
           const float inv = 1.0f / len;
           float tinv[TET_NID];
