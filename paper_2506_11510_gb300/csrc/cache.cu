@@ -610,11 +610,8 @@ template <bool COMPOSE>
 void launch_infer(const float* P, float* rec, long long n, float* y, cudaStream_t st) {
   if (n <= 0) return;
   const size_t shm = sizeof(InferSmem);
-  static bool attr = false;
-  if (!attr) {
-    TV_CUDA(cudaFuncSetAttribute(k_mlp_infer<COMPOSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    attr = true;
-  }
+  // per device and cheap: set on every launch
+  TV_CUDA(cudaFuncSetAttribute(k_mlp_infer<COMPOSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   int per_sm = 0;
   TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_infer<COMPOSE>, MT, shm));
   if (per_sm < 1) per_sm = 1;
@@ -717,11 +714,7 @@ int rc_mlp_grad(const float* params, const float* samples, int64_t n, float* gra
   if (n == 0) return TG_OK;
   try {
     const size_t shm = sizeof(rc::GradSmem);
-    static bool attr = false;
-    if (!attr) {
-      TV_CUDA(cudaFuncSetAttribute(rc::k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      attr = true;
-    }
+    TV_CUDA(cudaFuncSetAttribute(rc::k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     const long long ntiles = (n + rc::MT - 1) / rc::MT;
     long long blocks = rc::sm_count();
     if (blocks > ntiles) blocks = ntiles;
