@@ -189,3 +189,43 @@ def test_henyey_greenstein_density_normalised(g):
     assert tot == pytest.approx(1.0, abs=1e-9)
     if g == 0:
         assert O.hg_pdf(0.0, 0.3) == pytest.approx(1 / (4 * math.pi))
+
+
+@pytest.mark.parametrize("heterogeneous", [False, True])
+def test_collision_distances_are_exponential(heterogeneous):
+    """Free flights (Algorithm 1, SampleFreePath + MarchThroughCells): in a medium
+    that is homogeneous along each ray, the distance s from the entry point to
+    the first collision, given a collision, has F(s) = (1 - e^{-mu s}) / (1 - e^{-mu l})
+    (l the chord); the probability transforms u = F(s) of all paths are uniform
+    (Kolmogorov-Smirnov).  The heterogeneous case has densities 0.2 and 0.8 in the
+    halves x < 1/2 and x >= 1/2 (cell faces lie on x = 1/2 at this depth) and uses
+    the rays that stay in one half, each with its own rate."""
+    rho, sig = 0.5, 3.0
+    n = 16
+    vol = np.full((n, n, n), rho, np.float32)
+    if heterogeneous:
+        vol[:, :, : n // 2] = 0.2
+        vol[:, :, n // 2:] = 0.8
+    g = O.Grid(vol, (0, 0, 0), 1 / n, theta=-1, max_depth=6)
+    cam = W.Camera((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0, 1, 0), 8.0, 40, 40)   # nearly parallel to +z
+    med = W.Medium(0.7, 0.0, sig, 4, (0, -1, 0), 0.0, 1.0)
+    px, py, sm = all_paths(cam, 32)
+    q = g.cache_paths(cam, med, 17, px, py, sm, cache_depth=1)["query"]
+    hit = q[:, 3] > 0
+    o, D = camera_rays(cam, 17, px, py, sm)
+    u = []
+    for i in np.nonzero(hit)[0]:
+        se = CK.slab(o, D[i], (1, 1, 1))
+        t_in, chord = se[0], se[1] - se[0]
+        xa, xb = (o + t_in * D[i])[0], (o + se[1] * D[i])[0]
+        if (xa < 0.5) != (xb < 0.5):
+            continue                                    # the ray crosses x = 1/2
+        x = q[i, 0:3]                                   # grid position (domain extent 1)
+        s = float(np.dot(x - (o + t_in * D[i]), D[i]))
+        xi = int(min(max(np.floor(xa * n), 0), n - 1))
+        mu = sig * float(vol[0, 0, xi])
+        u.append((1 - math.exp(-mu * s)) / (1 - math.exp(-mu * chord)))
+    u = np.array(u)
+    assert len(u) > 10000
+    assert np.all((u >= 0) & (u <= 1 + 1e-12))
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
