@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--no-rebuild", action="store_true", help="skip the moved-camera rebuild leg")
     p.add_argument("--no-batch", action="store_true", help="skip the batched heterogeneous leg")
     p.add_argument("--batch-jobs", type=int, default=64)
-    p.add_argument("--cache-train-rounds", default="8,32,128", help="training budgets (rounds of 2^16 samples)")
+    p.add_argument("--cache-train-rounds", default="2,4,8,32,128", help="training budgets (rounds of 2^16 samples)")
     p.add_argument("--cache-ref-pixels", type=int, default=4096)
     p.add_argument("--cache-ref-spp", type=int, default=4096)
     return p.parse_args()
