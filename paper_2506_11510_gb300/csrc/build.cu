@@ -324,25 +324,38 @@ __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo
   L.cnt[i] = 0; L.sum[i] = 0; L.mn[i] = 0xFFFFFFFFu; L.mx[i] = 0;
 }
 
+// A3 statistics, between the passes: the leaf (position in the scan list) that
+// owns each work item, so that a work item finds its leaf with one load.
+__global__ void k_chunk_owner(const unsigned long long* __restrict__ chunk_off, long long m, int* __restrict__ owner) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const unsigned long long c1 = chunk_off[j + 1];
+  for (unsigned long long c = chunk_off[j]; c < c1; ++c) owner[c] = (int)j;
+}
+
+// Accumulate the voxels [a + lane + 32 s, b] of one row (the warp reads them along x).
+__device__ __forceinline__ void row_tail(const uint32_t* __restrict__ row, int a, int b, unsigned lane, uint32_t& cnt,
+                                         unsigned long long& sum, uint32_t& mn, uint32_t& mx) {
+  for (int ii = a + (int)lane; ii <= b; ii += 32) {
+    const uint32_t v = __ldg(row + ii);
+    ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+  }
+}
+
 // A3 statistics, pass 2 (leaves with larger boxes): one warp per ROWS rows
 // (along x) of a leaf's voxel box, one row interval per lane (row_interval), so
-// only the voxels inside are read: by the whole warp along each row in turn when
-// the box is at least 32 voxels wide (coalesced), else by each lane along its row.
+// only the voxels inside are read: by the whole warp along the rows when the box
+// is at least 32 voxels wide (coalesced; the first 32 voxels of four rows are
+// loaded together), else by each lane along its row.
 template <bool BOX>
 __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long* list, long long m,
-                                                    const unsigned long long* chunk_off, unsigned long long total,
-                                                    const uint32_t* __restrict__ q, Geo g) {
+                                                    const unsigned long long* chunk_off, const int* __restrict__ owner,
+                                                    unsigned long long total, const uint32_t* __restrict__ q, Geo g) {
   const unsigned lane = threadIdx.x & 31u;
   const long long warps = (long long)gridDim.x * (TPB / 32);
   const int hs = g.K - g.m - 1;                     // h = 2^hs
   for (long long c = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5); c < (long long)total; c += warps) {
-    // leaf j: last chunk_off[j] <= c
-    long long lo_j = 0, hi_j = m;
-    while (lo_j < hi_j) {
-      const long long mid = (lo_j + hi_j) >> 1;
-      if (chunk_off[mid] <= (unsigned long long)c) lo_j = mid + 1; else hi_j = mid;
-    }
-    const long long j = lo_j - 1;
+    const long long j = owner[c];                   // chunk_off[j] <= c < chunk_off[j + 1]
     const long long i = list ? list[j] : j;
     int x[4][3], lo[3], hi[3];
     load_tet(L.v, i, x);
@@ -367,17 +380,28 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long*
       rowoff = ((long long)kk * g.ny + jj) * g.nx;
     }
     if (hi[0] - lo[0] >= 31) {
-      // wide box: the warp reads one row at a time, lanes along x (coalesced)
-      for (int k = 0; k < 32; ++k) {
-        const int a = __shfl_sync(~0u, xa, k), b = __shfl_sync(~0u, xb, k);
-        const long long ro = __shfl_sync(~0u, rowoff, k);
-        for (int ii = a + (int)lane; ii <= b; ii += 32) {
-          const uint32_t v = __ldg(q + ro + ii);
-          ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+      // wide box: lanes along x (coalesced), four rows at a time
+      for (int k = 0; k < 32; k += 4) {
+        int a[4], b[4];
+        long long ro[4];
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = __shfl_sync(~0u, xa, k + u);
+          b[u] = __shfl_sync(~0u, xb, k + u);
+          ro[u] = __shfl_sync(~0u, rowoff, k + u);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = a[u] + (int)lane <= b[u] ? __ldg(q + ro[u] + a[u] + (int)lane) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (a[u] + (int)lane <= b[u]) { ++cnt; sum += v[u]; mn = min(mn, v[u]); mx = max(mx, v[u]); }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) row_tail(q + ro[u], a[u] + 32, b[u], lane, cnt, sum, mn, mx);
       }
     } else {
       // narrow box: one row per lane
+#pragma unroll 4
       for (int ii = xa; ii <= xb; ++ii) {
         const uint32_t v = __ldg(q + rowoff + ii);
         ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
@@ -800,7 +824,20 @@ struct Scanner {
   }
 };
 
-// Statistics and criterion of m new leaves (list == nullptr: leaves 0..m-1).
+// Pass 2 of the statistics over `total` work items (offsets off[0..m]): the
+// owner of every work item, then the scan.
+template <bool BOX>
+void stats_scan(LeafPtrs L, const long long* list, long long m, const unsigned long long* off,
+                unsigned long long total, DevBuf<int>& owner, const uint32_t* q, const Geo& g, int sms,
+                cudaStream_t st) {
+  owner.ensure(total);
+  k_chunk_owner<<<blocks_for(m), TPB, 0, st>>>(off, m, owner.p);
+  TV_LAUNCH();
+  const long long wblocks = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
+  k_stats_scan<BOX><<<(unsigned)wblocks, TPB, 0, st>>>(L, list, m, off, owner.p, total, q, g);
+  TV_LAUNCH();
+}
+
 // Scratch of the rebuild's statistics lookup
 struct LookupBufs {
   DevBuf<uint8_t> known;
@@ -813,7 +850,7 @@ struct LookupBufs {
 // only the others are scanned.
 void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const uint32_t* q, const Crit& C,
                          Scanner& scan, DevBuf<unsigned long long>& chunks, DevBuf<unsigned long long>& off,
-                         cudaStream_t st, int sms, const PrevNodes* prev, LookupBufs& lk) {
+                         DevBuf<int>& owner, cudaStream_t st, int sms, const PrevNodes* prev, LookupBufs& lk) {
   if (m == 0) return;
   LeafPtrs L = Lv.ptrs();
   const long long* slist = list;              // leaves to scan
@@ -847,12 +884,7 @@ void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const u
     unsigned long long total = 0;
     TV_CUDA(cudaMemcpyAsync(&total, off.p + sm, sizeof total, cudaMemcpyDeviceToHost, st));
     TV_CUDA(cudaStreamSynchronize(st));
-    if (total) {
-      const long long wblocks =
-          std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
-      k_stats_scan<false><<<(unsigned)wblocks, TPB, 0, st>>>(L, slist, sm, off.p, total, q, C.g);
-      TV_LAUNCH();
-    }
+    if (total) stats_scan<false>(L, slist, sm, off.p, total, owner, q, C.g, sms, st);
   }
   k_stats_finish<<<blocks_for(m), TPB, 0, st>>>(L, list, m, q, C, known);
   TV_LAUNCH();
@@ -956,12 +988,13 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
 
   Scanner scan;
   DevBuf<unsigned long long> chunks, off, marks, pos;
+  DevBuf<int> owner;
   DevBuf<long long> newlist;
   // interior nodes, appended as leaves are split
   DevBuf<unsigned long long> acode, asum;
   DevBuf<uint32_t> acnt, amn, amx;
   long long nint = 0;
-  stats_and_criterion(A, nullptr, nroots, q.p, C, scan, chunks, off, st, sms, pp, lk);
+  stats_and_criterion(A, nullptr, nroots, q.p, C, scan, chunks, off, owner, st, sms, pp, lk);
 
   long long N = nroots;
   const int max_rounds = 4 * max_depth + 16;
@@ -1018,7 +1051,7 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     std::swap(A, B);
     N += M;
     nint += M;
-    stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, st, sms, pp, lk);
+    stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, owner, st, sms, pp, lk);
   }
 
   // ---- interior-node statistics sorted by code (for rebuilds) ----
@@ -1134,6 +1167,7 @@ int grid_channels(GridImpl& G, const float* density, const float* temperature, c
   const long long nvox = (long long)g.nx * g.ny * g.nz;
   DevBuf<uint32_t> q(nvox), cnt(N), mn(N), mx(N);
   DevBuf<unsigned long long> sum(N), chunks, off;
+  DevBuf<int> owner;
   DevBuf<float> chan((size_t)N * 4), vmaj(N);
   TV_CUDA(cudaMemsetAsync(chan.p, 0, (size_t)N * 16, st));
   LeafPtrs L{reinterpret_cast<int4*>(G.verts), G.codes, nullptr, cnt.p, mn.p, mx.p, sum.p, nullptr};
@@ -1151,10 +1185,8 @@ int grid_channels(GridImpl& G, const float* density, const float* temperature, c
     TV_CUDA(cudaMemcpyAsync(&total, off.p + N, sizeof total, cudaMemcpyDeviceToHost, st));
     TV_CUDA(cudaStreamSynchronize(st));
     if (total) {
-      const long long wb = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
-      if (box) k_stats_scan<true><<<(unsigned)wb, TPB, 0, st>>>(L, nullptr, N, off.p, total, q.p, g);
-      else k_stats_scan<false><<<(unsigned)wb, TPB, 0, st>>>(L, nullptr, N, off.p, total, q.p, g);
-      TV_LAUNCH();
+      if (box) stats_scan<true>(L, nullptr, N, off.p, total, owner, q.p, g, sms, st);
+      else stats_scan<false>(L, nullptr, N, off.p, total, owner, q.p, g, sms, st);
     }
     if (box) k_leaf_small<true><<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g);
     else k_leaf_small<false><<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g);
