@@ -64,3 +64,100 @@ def test_sample_ranges_are_disjoint_and_cover():
     assert sorted(seen) == list(range(world * spp))
     with pytest.raises(ValueError):
         sharding.sample_range(4, 4, 1)
+
+
+# ---- failure detection and recovery (host only: ranks are CPU processes) ----
+
+def _resilient_main(rank, world, port, folder, spp, fail_after, out_path):
+    import datetime
+    import oracle as O
+    from paper_2506_11510_gb300 import workloads as W
+    from tests.conftest import scene_volume
+    store = dist.TCPStore("127.0.0.1", port, None, False, datetime.timedelta(seconds=30))
+    s = W.scene("tiny")
+    g = O.Grid.for_scene(s, scene_volume("tiny"))
+    rendered = []
+
+    def render(off, n):
+        rendered.append(off)
+        img, img2, _ = g.render(s.camera, s.medium, n, s.render_seed, sample_offset=off, nthreads=1)
+        return img, img2
+
+    try:
+        frame = sharding.render_resilient(rank, world, store, render, spp, 1, folder, timeout_s=1.0, poll_s=0.02,
+                                          give_up_s=60.0, fail_after=fail_after)
+    finally:
+        np.save(out_path + ".rendered%d.npy" % rank, np.array(rendered, dtype=np.int64))
+    np.save(out_path + ".frame%d.npy" % rank, np.stack(frame))
+
+
+def _run_ranks(world, folder, spp, fail_after, out_path):
+    import datetime
+    import multiprocessing
+    store = dist.TCPStore("127.0.0.1", 0, None, True, datetime.timedelta(seconds=30), wait_for_workers=False)
+    ctx = multiprocessing.get_context("spawn")
+    procs = [ctx.Process(target=_resilient_main, args=(r, world, store.port, folder, spp, fail_after.get(r), out_path))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    codes = [p.exitcode for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    return codes
+
+
+def _reference(spp):
+    import oracle as O
+    from paper_2506_11510_gb300 import workloads as W
+    from tests.conftest import scene_volume
+    s = W.scene("tiny")
+    g = O.Grid.for_scene(s, scene_volume("tiny"))
+    ref, ref2, _ = g.render(s.camera, s.medium, spp, s.render_seed, sample_offset=0, nthreads=2)
+    return ref, ref2
+
+
+def test_chunks_cover_the_frame():
+    assert sharding.frame_chunks(10, 4) == [(0, 4), (4, 4), (8, 2)]
+    assert sharding.frame_chunks(0, 3) == []
+    with pytest.raises(ValueError):
+        sharding.frame_chunks(4, 0)
+
+
+def test_a_rank_that_dies_mid_frame_is_taken_over(tmp_path):
+    """Three ranks; rank 2 raises after saving one of its three chunks.  The others
+    see its heartbeat stop, claim its two unfinished chunks, and every surviving
+    rank returns exactly the frame one process renders."""
+    import oracle as O
+    O.build()
+    spp, out = 9, str(tmp_path / "out")
+    codes = _run_ranks(3, str(tmp_path / "chunks"), spp, {2: 1}, out)
+    assert codes[0] == 0 and codes[1] == 0 and codes[2] != 0, codes
+    ref, ref2 = _reference(spp)
+    for r in (0, 1):
+        got = np.load(out + ".frame%d.npy" % r)
+        assert np.allclose(got[0], ref, rtol=1e-12, atol=1e-14)
+        assert np.allclose(got[1], ref2, rtol=1e-12, atol=1e-14)
+    done = [np.load(out + ".rendered%d.npy" % r) for r in range(3)]
+    assert sorted(np.concatenate(done).tolist()) == list(range(spp))   # every chunk rendered once
+    assert done[2].tolist() == [2]
+
+
+def test_a_restarted_job_resumes_from_its_saved_chunks(tmp_path):
+    """Every rank fails after one chunk; the restarted job renders only the chunks
+    that were not saved, and the frame equals one process rendering all of it."""
+    import oracle as O
+    O.build()
+    spp, folder, out = 8, str(tmp_path / "chunks"), str(tmp_path / "out")
+    codes = _run_ranks(2, folder, spp, {0: 1, 1: 1}, out + "a")
+    assert all(c != 0 for c in codes), codes
+    codes = _run_ranks(2, folder, spp, {}, out + "b")
+    assert codes == [0, 0], codes
+    again = np.concatenate([np.load(out + "b.rendered%d.npy" % r) for r in range(2)])
+    assert sorted(again.tolist()) == [2, 3, 4, 5, 6, 7]                  # chunks 0 and 1 were kept
+    ref, ref2 = _reference(spp)
+    got = np.load(out + "b.frame0.npy")
+    assert np.allclose(got[0], ref, rtol=1e-12, atol=1e-14)
+    assert np.allclose(got[1], ref2, rtol=1e-12, atol=1e-14)
