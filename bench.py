@@ -103,6 +103,10 @@ class ClockSampler:
         self.out.seek(0)
         rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
         self.out.close()
+        try:
+            os.remove(self.out.name)
+        except OSError:
+            pass
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
