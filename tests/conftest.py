@@ -30,3 +30,28 @@ def scene_volume(name, **kw):
 @pytest.fixture(scope="session")
 def tiny_volume():
     return scene_volume("tiny")
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def paper_count(name):
+    """A count the paper states about its grids (tests/golden/paper_counts.txt)."""
+    with open(os.path.join(GOLDEN, "paper_counts.txt")) as fh:
+        for line in fh:
+            f = line.split()
+            if f and not f[0].startswith("#") and f[0] == name:
+                return int(f[1])
+    raise KeyError(name)
+
+
+def control_cube_tets():
+    """The paper's 24 control-cube tetrahedra (tests/golden/control_cube_24_tets.txt): a list
+    of frozensets of 4 points, in units of half the cube edge."""
+    out = []
+    with open(os.path.join(GOLDEN, "control_cube_24_tets.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                v = [int(x) for x in line.split()]
+                out.append(frozenset(tuple(v[3 * k:3 * k + 3]) for k in range(4)))
+    return out

@@ -12,7 +12,7 @@ import torch
 import oracle as O
 from paper_2506_11510_gb300 import workloads as W
 from tests import _checks as CK
-from tests.conftest import scene_volume
+from tests.conftest import control_cube_tets, paper_count, scene_volume
 
 
 def uniform_grid(dims, depth, value=0.5):
@@ -34,7 +34,8 @@ def test_tiny_scene_is_uniform_depth_12(tiny_volume):
     a = O.Grid.for_scene(s, tiny_volume).export()
     assert len(a.codes) == 24576                     # 6 * 2^12
     CK.check_grid(a)
-    assert set(np.unique(a.nid)) == set(range(18))   # Sec. 3: 18 face orientations
+    assert set(np.unique(a.nid)) == set(range(paper_count("face_orientations")))   # Sec. 3
+    assert a.nbr.shape[1] == paper_count("max_neighbours")
 
 
 def test_depth2_is_the_24_halfedge_control_cube():
@@ -43,7 +44,13 @@ def test_depth2_is_the_24_halfedge_control_cube():
     g = uniform_grid((8, 8, 8), 2)
     a = g.export()
     S = 1 << a.K
-    assert len(a.codes) == 24
+    assert len(a.codes) == paper_count("control_cube_tets")
+    # the same tetrahedra as the paper's list (tests/golden), vertex sets compared
+    want = control_cube_tets()
+    assert len(want) == len(set(want)) == paper_count("control_cube_tets")
+    got = {frozenset(tuple(int(c) // (S // 2) for c in v) for v in T) for T in a.verts}
+    assert all(int(c) % (S // 2) == 0 for T in a.verts for v in T for c in v)
+    assert got == set(want)
     seen = set()
     for T in a.verts:
         pts = {tuple(int(c) for c in v) for v in T}
