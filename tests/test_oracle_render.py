@@ -229,3 +229,26 @@ def test_collision_distances_are_exponential(heterogeneous):
     assert len(u) > 10000
     assert np.all((u >= 0) & (u <= 1 + 1e-12))
     assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+@pytest.mark.parametrize("kind", ["tet", "dda"])
+def test_image_orientation(kind):
+    """The pixel convention (y down, right = forward x up): a camera on the -z side
+    looking along +z with up +y sees world x < 1/2 on the right of the image and
+    y > 1/2 in its top rows.  An absorbing block filling x < 1/2, y > 1/2 through
+    the whole depth darkens exactly the top-right quadrant; every other ray crosses
+    empty space and returns the environment, 1.  A mirrored axis or a flipped row
+    order anywhere in the camera model moves the dark quadrant."""
+    vol = np.zeros((16, 16, 16), np.float32)
+    vol[:, 8:, :8] = 1.0                                  # [z][y][x]: y > 1/2, x < 1/2
+    cam = W.Camera((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0, 1, 0), 30.0, 12, 16)   # every ray meets the front face
+    med = W.Medium(0.0, 0.0, 60.0, 4, (0.0, -1.0, 0.0), 0.0, 1.0)
+    px, py, sm = all_paths(cam, 2)
+    if kind == "tet":
+        L = O.Grid(vol, (0, 0, 0), 1 / 16, theta=0.1, max_depth=9).render_paths(cam, med, 5, px, py, sm)["L"]
+    else:
+        L = O.dda_render_paths(vol, (0, 0, 0), 1 / 16, cam, med, 5, px, py, sm)["L"]
+    right, top = px >= cam.width // 2, py < cam.height // 2
+    dark = right & top
+    assert np.all(L[~dark] == 1.0)
+    assert L[dark].max() < 1e-6
