@@ -181,6 +181,15 @@ def test_henyey_greenstein_sampling(g):
     keep = exp > 5
     chi2 = np.sum((obs[keep] - exp[keep]) ** 2 / exp[keep])
     assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4
+    # the azimuth about d is uniform (any orthonormal frame of d: here Gram-Schmidt on e_x or e_y)
+    a = np.array([1.0, 0.0, 0.0]) if abs(d[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    t = a - (a @ d) * d; t /= np.linalg.norm(t)
+    b = np.cross(d, t)
+    W_ = np.array([O.hg_sample(g, u[i, 0], u[i, 1], d) for i in range(n)])
+    phi = np.mod(np.arctan2(W_ @ b, W_ @ t), 2 * math.pi)
+    obs, _ = np.histogram(phi, np.linspace(0, 2 * math.pi, 17))
+    chi2 = np.sum((obs - n / 16) ** 2 / (n / 16))
+    assert stats.chi2.sf(chi2, 15) > 1e-4
 
 
 @pytest.mark.parametrize("g", [-0.5, 0.0, 0.3, 0.95])
@@ -252,3 +261,20 @@ def test_image_orientation(kind):
     dark = right & top
     assert np.all(L[~dark] == 1.0)
     assert L[dark].max() < 1e-6
+
+
+def test_albedo_multiplies_once_per_collision():
+    """No sun, environment 1: a path that escapes after k collisions returns exactly
+    albedo^k (the throughput is multiplied by the albedo at every collision), and a
+    truncated path returns 0."""
+    vol = _homog(value=0.8)
+    cam = W.Camera((0.5, 0.6, -1.5), (0.5, 0.5, 0.5), (0, 1, 0), 30.0, 16, 16)
+    alb = 0.75
+    med = W.Medium(alb, 0.2, 6.0, 12, (0.0, -1.0, 0.0), 0.0, 1.0)
+    px, py, sm = all_paths(cam, 8)
+    res = O.Grid(vol, (0, 0, 0), 1 / 16, theta=-1, max_depth=6).render_paths(cam, med, 13, px, py, sm)
+    trunc = (res["flags"] & 2) != 0
+    k = res["collisions"][~trunc].astype(np.int64)
+    assert k.max() >= 4 and trunc.any()
+    assert np.allclose(res["L"][~trunc], alb ** k, rtol=1e-12, atol=0)
+    assert np.all(res["L"][trunc] == 0.0)
