@@ -616,10 +616,12 @@ def oracle_window_render(s, g, wcam, min_seconds=10.0, nthreads=0):
 
 
 def cpu_sample_text(side, s, paths, tb):
+    grid = ("on the oracle's grid refined for the window's sub-frustum only (coarse elsewhere, so paths are "
+            "cheaper than the full frame's" if s.footprint_px > 0 else
+            "on the oracle's grid (the same grid as the full frame's: no camera criterion")
     return ("%dx%d-pixel window at the frame centre, %d spp per frame, %d paths over successive sample ranges, "
-            "on the oracle's grid refined for the window's sub-frustum only (coarse elsewhere, so paths are "
-            "cheaper than the full frame's; built once in %.0f s, not timed); fp64 C++, OpenMP over paths"
-            % (side, side, s.spp, paths, tb))
+            "%s; built once in %.0f s, not timed); fp64 C++, OpenMP over paths"
+            % (side, side, s.spp, paths, grid, tb))
 
 
 def cpu_baseline(args, s, vol):
