@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched heterogeneous leg")
     p.add_argument("--batch-jobs", type=int, default=64)
     p.add_argument("--cache-train-rounds", default="2,4,8,32,128", help="training budgets (rounds of 2^16 samples)")
+    p.add_argument("--cache-train-bounces", default="16,32",
+                   help="collision limits of training paths tried besides the medium's (empty: none)")
     p.add_argument("--cache-ref-pixels", type=int, default=4096)
     p.add_argument("--cache-ref-spp", type=int, default=4096)
     return p.parse_args()
@@ -536,22 +538,43 @@ def cache_leg(args, s, grid, dev, plain_ms):
            "reference_ms": round(ref_ms, 1), "rms_radiance": round(rel, 6),
            "plain": {"spp": s.spp, "ms": round(plain_ms, 2), "rmse": round(target, 6)}, "variants": []}
     best = None
+
+    def variant(rounds, depth, train_bounces=None):
+        rc = RC.RadianceCache(W.mlp_init_params(1, b4=0.1), device=dev, lr=3e-3)
+        _, train_ms = timed(lambda: rc.train(grid, s.camera, s.medium, s.render_seed, rounds=rounds,
+                                             max_bounces=train_bounces))
+        curve, reached = [], None
+        for spp in (1, 2, 4, 8, 16, 32):
+            (img, _), ms = timed(lambda: rc.render(grid, s.camera, s.medium, spp, s.render_seed, depth))
+            e = rmse(img, spp)
+            curve.append({"spp": spp, "ms": round(ms, 2), "rmse": round(e, 6)})
+            if reached is None and e <= target:
+                reached = train_ms + ms
+        v = {"cache_depth": depth, "train_rounds": rounds, "train_samples_per_round": (1 << 14) * 4,
+             "train_max_bounces": train_bounces or s.medium.max_bounces,
+             "adam_steps": rc.step, "train_ms": round(train_ms, 2),
+             "final_train_loss": round(float(rc.loss[2]), 6), "curve": curve,
+             "time_to_equal_rmse_ms": None if reached is None else round(reached, 2),
+             "speedup_vs_plain": None if reached is None else round(plain_ms / reached, 3)}
+        return v, reached
+
     for rounds in [int(r) for r in str(args.cache_train_rounds).split(",") if r]:
         for depth in (1, 2):
-            rc = RC.RadianceCache(W.mlp_init_params(1, b4=0.1), device=dev, lr=3e-3)
-            _, train_ms = timed(lambda: rc.train(grid, s.camera, s.medium, s.render_seed, rounds=rounds))
-            curve, reached = [], None
-            for spp in (1, 2, 4, 8, 16, 32):
-                (img, _), ms = timed(lambda: rc.render(grid, s.camera, s.medium, spp, s.render_seed, depth))
-                e = rmse(img, spp)
-                curve.append({"spp": spp, "ms": round(ms, 2), "rmse": round(e, 6)})
-                if reached is None and e <= target:
-                    reached = train_ms + ms
-            v = {"cache_depth": depth, "train_rounds": rounds, "train_samples_per_round": (1 << 14) * 4,
-                 "adam_steps": rc.step, "train_ms": round(train_ms, 2),
-                 "final_train_loss": round(float(rc.loss[2]), 6), "curve": curve,
-                 "time_to_equal_rmse_ms": None if reached is None else round(reached, 2),
-                 "speedup_vs_plain": None if reached is None else round(plain_ms / reached, 3)}
+            v, reached = variant(rounds, depth)
+            res["variants"].append(v)
+            if reached is not None and (best is None or reached < best):
+                best = reached
+    # training paths cut at fewer collisions than the rendered ones (the training
+    # launch then ends with its longest path of that length); guarded so that a
+    # failing variant is reported instead of ending the benchmark
+    for tb in [int(b) for b in str(args.cache_train_bounces).split(",") if b]:
+        for rounds in (4, 8):
+            try:
+                v, reached = variant(rounds, 1, tb)
+            except Exception as exc:                      # noqa: BLE001
+                res["variants"].append({"cache_depth": 1, "train_rounds": rounds, "train_max_bounces": tb,
+                                        "error": str(exc)[:200]})
+                continue
             res["variants"].append(v)
             if reached is not None and (best is None or reached < best):
                 best = reached

@@ -8,6 +8,8 @@ the tracer, the fused tensor-core MLP kernels and Adam all run there.
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
+import types
 from typing import Optional
 
 import torch
@@ -98,6 +100,19 @@ def render_cached(grid: Grid, camera, medium, spp: int, seed: int, cache_depth: 
     return s, s2
 
 
+def with_max_bounces(medium, max_bounces: int):
+    """The medium with another collision limit (training paths may be cut shorter
+    than the rendered ones)."""
+    if int(max_bounces) < 1:
+        raise ValueError("max_bounces must be >= 1")
+    if dataclasses.is_dataclass(medium):
+        return dataclasses.replace(medium, max_bounces=int(max_bounces))
+    fields = ("albedo", "g", "sigma_scale", "max_bounces", "sun_dir", "sun_irradiance", "env_radiance")
+    d = {k: getattr(medium, k) for k in fields}
+    d["max_bounces"] = int(max_bounces)
+    return types.SimpleNamespace(**d)
+
+
 def timeouts() -> int:
     c = C.c_int64()
     N.check(N.lib().rc_timeouts(C.byref(c)), "rc_timeouts")
@@ -124,11 +139,17 @@ class RadianceCache:
         self._buf = None
 
     def train(self, grid: Grid, camera, medium, seed: int, rounds: int = 1, first_round: int = 0,
-              n_paths: int = 1 << 14, max_vertices: int = 4, batches: int = 4, sample_base: int = 1 << 24):
+              n_paths: int = 1 << 14, max_vertices: int = 4, batches: int = 4, sample_base: int = 1 << 24,
+              max_bounces: Optional[int] = None):
         """`rounds` training rounds: each traces n_paths full paths at uniform
         pixels (sample indices disjoint from rendering's) and takes `batches`
         Adam steps on their n_paths * max_vertices vertex samples.  The paths
-        of all rounds are traced in one launch, then the steps run in order."""
+        of all rounds are traced in one launch, then the steps run in order.
+        max_bounces, when given, cuts the training paths at that many collisions
+        (their targets then miss what lies beyond; the launch no longer waits
+        for the longest paths of the medium's own limit)."""
+        if max_bounces is not None:
+            medium = with_max_bounces(medium, max_bounces)
         total = rounds * n_paths
         px, py, sm = random_paths(seed ^ (0x9E3779B97F4A7C15 * (first_round + 1) & 0xFFFFFFFFFFFFFFFF), total,
                                   camera.width, camera.height,

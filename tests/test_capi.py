@@ -117,3 +117,20 @@ def test_rebuild_batch_and_channel_argument_checks_need_no_gpu():
                             None) == N.TG_EINVAL
     assert L.tet_trace_ext_paths(None, C.byref(cam), C.byref(med), C.byref(ext), 0, 1, fake, fake, fake, None,
                                  None, None, None, None) == N.TG_EINVAL
+
+
+def test_training_bounce_limit_changes_only_the_limit():
+    """RadianceCache.train(max_bounces=k) traces its training paths in the same
+    medium with the collision limit k (host logic, no GPU)."""
+    import types
+    from paper_2506_11510_gb300 import cache as RC, workloads as W
+    m = W.scene("production").medium
+    c = RC.with_max_bounces(m, 16)
+    assert c.max_bounces == 16 and m.max_bounces == 128
+    assert (c.albedo, c.g, c.sigma_scale, c.sun_dir, c.sun_irradiance, c.env_radiance) == \
+        (m.albedo, m.g, m.sigma_scale, m.sun_dir, m.sun_irradiance, m.env_radiance)
+    o = types.SimpleNamespace(albedo=.5, g=.1, sigma_scale=2., max_bounces=9, sun_dir=(0, 0, 1), sun_irradiance=1.,
+                              env_radiance=0.)
+    assert RC.with_max_bounces(o, 3).max_bounces == 3 and o.max_bounces == 9
+    with pytest.raises(ValueError):
+        RC.with_max_bounces(m, 0)
