@@ -21,7 +21,17 @@
 //  * Henyey-Greenstein phase function, sun next-event estimation, constant
 //    environment on escape, Philox4x32-10 random numbers (not in the paper).
 //
-// Parity pins live in the tests; functions with no pin are marked there.
+// Pins (tests/test_oracle_*.py) tie each part to something other than this
+// file: Philox to cuRAND's generator; roots, bisection, closure and statistics
+// to the paper's control cube (tests/golden), exact volumes, conformity,
+// brute-force voxel sums and a random-order closure; the walk to clipping the
+// ray with every tetrahedron; free flights to the exponential law (KS);
+// transmittance, single scattering and the throughput rule to closed forms; HG
+// sampling to its density; the camera model to an absorbing-block image.
+// Partly pinned: the camera criterion's footprint threshold (bounds and
+// monotonicity only).  Parity unpinned: multiple scattering in a heterogeneous
+// medium as a whole has no closed form; beyond its pinned steps it is checked
+// only by the white furnace and by agreement with the DDA tracker.
 
 #include "oracle.h"
 
