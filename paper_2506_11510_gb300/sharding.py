@@ -102,6 +102,8 @@ def render_resilient(rank: int, world_size: int, store, render, spp: int, chunk_
     the host, for tests).  Raises TimeoutError when no chunk completes for
     give_up_s."""
     chunks = frame_chunks(spp, chunk_spp)
+    if not chunks or world_size < 1 or not 0 <= rank < world_size:
+        raise ValueError("bad spp / rank / world size")
     files = ChunkFiles(folder)
     me = str(rank)
     saved = 0

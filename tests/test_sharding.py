@@ -119,11 +119,15 @@ def _reference(spp):
     return ref, ref2
 
 
-def test_chunks_cover_the_frame():
+def test_chunks_cover_the_frame(tmp_path):
     assert sharding.frame_chunks(10, 4) == [(0, 4), (4, 4), (8, 2)]
     assert sharding.frame_chunks(0, 3) == []
     with pytest.raises(ValueError):
         sharding.frame_chunks(4, 0)
+    with pytest.raises(ValueError):
+        sharding.render_resilient(0, 1, None, None, 0, 1, str(tmp_path))      # an empty frame
+    with pytest.raises(ValueError):
+        sharding.render_resilient(2, 2, None, None, 4, 1, str(tmp_path))      # rank out of range
 
 
 def test_a_rank_that_dies_mid_frame_is_taken_over(tmp_path):
