@@ -89,12 +89,43 @@ def _host(t):
     return np.asarray(t)
 
 
+class LocalStore:
+    """The store operations render_resilient uses, in one process (world size 1)."""
+
+    def __init__(self):
+        self.kv = {}
+
+    def set(self, key, value):
+        self.kv[key] = value.encode() if isinstance(value, str) else bytes(value)
+
+    def get(self, key):
+        return self.kv[key]
+
+    def check(self, keys):
+        return all(k in self.kv for k in keys)
+
+    def add(self, key, n):
+        v = int(self.kv.get(key, b"0")) + int(n)
+        self.kv[key] = str(v).encode()
+        return v
+
+    def compare_set(self, key, expected, desired):
+        # as torch.distributed.TCPStore: set when the key holds `expected` (or is
+        # absent and `expected` is empty); return the value now held, or `expected`
+        # for an absent key that stays absent
+        cur = self.kv.get(key)
+        if (cur is None and expected == "") or (cur is not None and cur.decode() == expected):
+            self.set(key, desired)
+        return self.kv.get(key, expected.encode())
+
+
 def render_resilient(rank: int, world_size: int, store, render, spp: int, chunk_spp: int, folder: str,
                      timeout_s: float = 30.0, poll_s: float = 0.05, give_up_s: float = 600.0, fail_after=None):
     """Render this rank's chunks of a frame and finish the chunks of ranks that stop.
 
     render(sample_offset, spp) -> (sum, sumsq) renders one chunk (per-pixel sums,
-    numpy or torch).  Chunk c belongs to rank c % world_size until another rank
+    numpy or torch).  With world_size 1 the store may be None: the chunk files
+    alone then give checkpoint and resume.  Chunk c belongs to rank c % world_size until another rank
     claims it.  Returns the frame's (sum, sumsq) as float64 arrays (the chunks
     added in order) once every chunk is saved.  timeout_s must exceed one chunk's
     render time: a rank's heartbeat moves once per chunk and once per poll.
@@ -104,6 +135,10 @@ def render_resilient(rank: int, world_size: int, store, render, spp: int, chunk_
     chunks = frame_chunks(spp, chunk_spp)
     if not chunks or world_size < 1 or not 0 <= rank < world_size:
         raise ValueError("bad spp / rank / world size")
+    if store is None:
+        if world_size != 1:
+            raise ValueError("several ranks need a shared store")
+        store = LocalStore()                         # one process: checkpoint and resume only
     files = ChunkFiles(folder)
     me = str(rank)
     saved = 0

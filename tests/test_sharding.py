@@ -165,3 +165,42 @@ def test_a_restarted_job_resumes_from_its_saved_chunks(tmp_path):
     got = np.load(out + "b.frame0.npy")
     assert np.allclose(got[0], ref, rtol=1e-12, atol=1e-14)
     assert np.allclose(got[1], ref2, rtol=1e-12, atol=1e-14)
+
+
+def test_one_process_resumes_from_its_chunk_files(tmp_path):
+    """World size 1 without a store: a run that fails after two chunks leaves them
+    on disk; the next run renders only the other chunks and returns the frame."""
+    import oracle as O
+    from paper_2506_11510_gb300 import workloads as W
+    from tests.conftest import scene_volume
+    O.build()
+    s = W.scene("tiny")
+    g = O.Grid.for_scene(s, scene_volume("tiny"))
+    done = []
+
+    def render(off, n):
+        done.append(off)
+        img, img2, _ = g.render(s.camera, s.medium, n, s.render_seed, sample_offset=off, nthreads=2)
+        return img, img2
+
+    folder = str(tmp_path / "chunks")
+    with pytest.raises(RuntimeError):
+        sharding.render_resilient(0, 1, None, render, 5, 1, folder, fail_after=2)
+    assert done == [0, 1]
+    frame = sharding.render_resilient(0, 1, None, render, 5, 1, folder)
+    assert done == [0, 1, 2, 3, 4]
+    ref, ref2 = _reference(5)
+    assert np.allclose(frame[0], ref, rtol=1e-12, atol=1e-14)
+    assert np.allclose(frame[1], ref2, rtol=1e-12, atol=1e-14)
+    with pytest.raises(ValueError):
+        sharding.render_resilient(0, 2, None, render, 5, 1, folder)           # two ranks need a store
+
+
+def test_local_store_claims_once():
+    st = sharding.LocalStore()
+    assert st.compare_set("claim/0", "", "1") == b"1"
+    assert st.compare_set("claim/0", "", "2") == b"1"                         # already claimed
+    assert st.compare_set("claim/0", "1", "2") == b"2"                        # taken over from rank 1
+    assert st.add("hb/0", 1) == 1 and st.add("hb/0", 0) == 1
+    assert st.check(["claim/0"]) and not st.check(["claim/1"])
+    assert st.compare_set("claim/1", "3", "4") == b"3" and not st.check(["claim/1"])
