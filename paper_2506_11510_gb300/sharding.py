@@ -60,7 +60,9 @@ def frame_chunks(spp: int, chunk_spp: int) -> list[tuple[int, int]]:
 
 
 class ChunkFiles:
-    """One file per finished chunk: its per-pixel sums (the checkpoint)."""
+    """One file per finished chunk: its per-pixel sums (the checkpoint) and the key
+    of the frame it belongs to (its sample range, the frame's spp and chunk size,
+    and a caller tag naming the seed, camera, grid and medium)."""
 
     def __init__(self, folder: str):
         self.folder = folder
@@ -72,15 +74,25 @@ class ChunkFiles:
     def has(self, c: int) -> bool:
         return os.path.exists(self.path(c))
 
-    def save(self, c: int, s, s2) -> None:
+    def save(self, c: int, s, s2, key: str = "") -> None:
         tmp = self.path(c) + ".tmp%d" % os.getpid()
         with open(tmp, "wb") as fh:
-            np.savez(fh, sum=_host(s), sumsq=_host(s2))
+            np.savez(fh, sum=_host(s), sumsq=_host(s2), key=np.array(key))
         os.replace(tmp, self.path(c))                # a chunk file is whole or absent
+
+    def key(self, c: int) -> str:
+        with np.load(self.path(c)) as z:
+            return str(z["key"]) if "key" in z.files else ""
 
     def load(self, c: int):
         with np.load(self.path(c)) as z:
             return z["sum"], z["sumsq"]
+
+
+def chunk_key(sample_offset: int, spp: int, chunk_spp: int, frame_spp: int, tag: str) -> str:
+    """The frame key saved with a chunk: a chunk file is only reused by a frame
+    whose key for that chunk is the same."""
+    return "offset=%d spp=%d chunk_spp=%d frame_spp=%d tag=%s" % (sample_offset, spp, chunk_spp, frame_spp, tag)
 
 
 def _host(t):
@@ -120,7 +132,8 @@ class LocalStore:
 
 
 def render_resilient(rank: int, world_size: int, store, render, spp: int, chunk_spp: int, folder: str,
-                     timeout_s: float = 30.0, poll_s: float = 0.05, give_up_s: float = 600.0, fail_after=None):
+                     timeout_s: float = 30.0, poll_s: float = 0.05, give_up_s: float = 600.0, fail_after=None,
+                     frame_tag: str = ""):
     """Render this rank's chunks of a frame and finish the chunks of ranks that stop.
 
     render(sample_offset, spp) -> (sum, sumsq) renders one chunk (per-pixel sums,
@@ -131,7 +144,13 @@ def render_resilient(rank: int, world_size: int, store, render, spp: int, chunk_
     render time: a rank's heartbeat moves once per chunk and once per poll.
     fail_after=k makes this rank raise after saving k chunks (fault injection on
     the host, for tests).  Raises TimeoutError when no chunk completes for
-    give_up_s."""
+    give_up_s.
+
+    Every chunk file carries the frame's key for it (chunk_key: its sample range,
+    spp, chunk_spp and frame_tag, which the caller sets to something naming the
+    seed, camera, medium and grid).  A saved chunk is reused only when its key is
+    this frame's; a folder holding chunks of another frame, or chunks of
+    different image shapes, raises ValueError instead of being summed in."""
     chunks = frame_chunks(spp, chunk_spp)
     if not chunks or world_size < 1 or not 0 <= rank < world_size:
         raise ValueError("bad spp / rank / world size")
@@ -146,13 +165,23 @@ def render_resilient(rank: int, world_size: int, store, render, spp: int, chunk_
     def beat():
         store.add("hb/%d" % rank, 1)
 
+    def own_key(c):
+        return chunk_key(chunks[c][0], chunks[c][1], chunk_spp, spp, frame_tag)
+
+    def check_key(c):
+        if files.key(c) != own_key(c):
+            raise ValueError("chunk file %s belongs to another frame (%r, this frame wants %r)"
+                             % (files.path(c), files.key(c), own_key(c)))
+
     def finish(c):
         nonlocal saved
-        if not files.has(c):                         # resuming: a saved chunk is kept
+        if files.has(c):                             # resuming: a saved chunk of this frame is kept
+            check_key(c)
+        else:
             if fail_after is not None and saved >= fail_after:
                 raise RuntimeError("rank %d: injected failure" % rank)
             s, s2 = render(*chunks[c])
-            files.save(c, s, s2)
+            files.save(c, s, s2, own_key(c))
             saved += 1
         store.set("done/%d" % c, me)
         beat()
@@ -191,7 +220,10 @@ def render_resilient(rank: int, world_size: int, store, render, spp: int, chunk_
 
     s = s2 = None
     for c in range(len(chunks)):
+        check_key(c)                                 # a chunk another rank saved, too
         a, b = files.load(c)
+        if s is not None and (a.shape != s.shape or b.shape != s2.shape):
+            raise ValueError("chunk %d has image shape %s, chunk 0 has %s" % (c, a.shape, s.shape))
         s = a.astype(np.float64) if s is None else s + a
         s2 = b.astype(np.float64) if s2 is None else s2 + b
     return s, s2

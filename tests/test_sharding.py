@@ -204,3 +204,37 @@ def test_local_store_claims_once():
     assert st.add("hb/0", 1) == 1 and st.add("hb/0", 0) == 1
     assert st.check(["claim/0"]) and not st.check(["claim/1"])
     assert st.compare_set("claim/1", "3", "4") == b"3" and not st.check(["claim/1"])
+
+
+def test_a_reused_folder_of_another_frame_is_refused(tmp_path):
+    """Chunk files carry their frame's key: a folder reused for a frame with another
+    seed (tag) or another chunk size raises instead of summing the old chunks in,
+    and the same frame still resumes from it."""
+    calls = []
+
+    def render(off, n):
+        calls.append((off, n))
+        v = np.full((3, 4), float(off + n), np.float32)
+        return v, v * v
+
+    folder = str(tmp_path / "chunks")
+    a = sharding.render_resilient(0, 1, None, render, 4, 2, folder, frame_tag="seed=7")
+    assert calls == [(0, 2), (2, 2)]
+    with pytest.raises(ValueError, match="another frame"):
+        sharding.render_resilient(0, 1, None, render, 4, 2, folder, frame_tag="seed=8")
+    with pytest.raises(ValueError, match="another frame"):
+        sharding.render_resilient(0, 1, None, render, 4, 1, folder, frame_tag="seed=7")
+    calls.clear()
+    b = sharding.render_resilient(0, 1, None, render, 4, 2, folder, frame_tag="seed=7")
+    assert calls == [] and np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_chunks_of_different_image_shapes_are_refused(tmp_path):
+    """Two chunks of one key but different image shapes (a corrupt or hand-edited
+    folder) raise ValueError rather than broadcasting."""
+    folder = str(tmp_path / "chunks")
+    files = sharding.ChunkFiles(folder)
+    files.save(0, np.zeros((2, 2)), np.zeros((2, 2)), sharding.chunk_key(0, 1, 1, 2, "t"))
+    files.save(1, np.zeros((3, 2)), np.zeros((3, 2)), sharding.chunk_key(1, 1, 1, 2, "t"))
+    with pytest.raises(ValueError, match="shape"):
+        sharding.render_resilient(0, 1, None, None, 2, 1, folder, frame_tag="t")
