@@ -165,7 +165,10 @@ void tg_grid_free(tg_grid* g);
  * caller-owned device float[H][W], never cleared by the call, so progressive
  * calls compose.  stats: device tg_stats or NULL.  Random numbers are Philox4x32-10,
  * key (seed lo, seed hi ^ pixel), counter (s, slot / 4, 0, 0).
- * Asynchronous.  Errors: TG_EINVAL, TG_ECUDA.  A walk that exceeds its step
+ * Asynchronous.  Errors: TG_EINVAL (also when sample_offset + spp > INT32_MAX:
+ * sample indices are int32, and the render, grid_render, tet_render_ext,
+ * tet_render_cached, tet_render_noalloc and batch entry points all refuse a range
+ * that would wrap), TG_ECUDA.  A walk that exceeds its step
  * limit ends its path and is counted in stats->step_limit.
  * Calls that overlap on the same grid share its scratch counter: serialise them.
  */

@@ -137,7 +137,7 @@ int tg_batch_create(const tg_job* jobs, int32_t njobs, int32_t autotune, void* c
   long long total = 0, maxpix = 0;
   for (int i = 0; i < njobs; ++i) {
     const tg_job& j = jobs[i];
-    if (!j.grid || !camera_ok(&j.cam) || !medium_ok(&j.med) || j.spp < 1 || j.sample_offset < 0 || !j.accum_sum)
+    if (!j.grid || !camera_ok(&j.cam) || !medium_ok(&j.med) || j.spp < 1 || !samples_ok(j.spp, j.sample_offset) || !j.accum_sum)
       return TG_EINVAL;
     if (j.grid->impl.n == 0) return TG_EINVAL;
     if (fmt >= 0 && j.grid->impl.fmt != fmt) return TG_EINVAL;   // one density format per batch

@@ -748,7 +748,7 @@ int rc_adam(float* params, float* m, float* v, float* grad, float* loss, int32_t
 int tet_render_cached(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp, uint64_t seed,
                       int32_t sample_offset, int32_t cache_depth, const float* params, float* accum_sum,
                       float* accum_sumsq, tg_stats* stats, void* cuda_stream) {
-  if (!g || !camera_ok(cam) || !medium_ok(med) || spp < 0 || sample_offset < 0 || cache_depth < 1 || !params ||
+  if (!g || !camera_ok(cam) || !medium_ok(med) || !samples_ok(spp, sample_offset) || cache_depth < 1 || !params ||
       !accum_sum)
     return TG_EINVAL;
   try {

@@ -267,6 +267,11 @@ struct MedF {
 CamF camera_setup(const tg_camera& c, const float box_min[3], double cube);
 MedF medium_setup(const tg_medium& m, double cube);
 bool camera_ok(const tg_camera* c);
+// A frame's sample indices [offset, offset + spp) must be non-negative int32
+// values: beyond INT32_MAX they would wrap and repeat other samples' streams.
+inline bool samples_ok(int32_t spp, int32_t offset) {
+  return spp >= 0 && offset >= 0 && (int64_t)offset + spp <= (int64_t)INT32_MAX;
+}
 bool medium_ok(const tg_medium* m);
 
 }  // namespace tv

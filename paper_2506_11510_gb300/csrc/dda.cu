@@ -59,7 +59,7 @@ int grid_render(const float* density, const tg_volume_desc* vol, const tg_camera
   VoxParams p;
   double cube;
   float bmin[3];
-  if (!density || !accum_sum || !camera_ok(cam) || !medium_ok(med) || spp < 0 || sample_offset < 0 ||
+  if (!density || !accum_sum || !camera_ok(cam) || !medium_ok(med) || !samples_ok(spp, sample_offset) ||
       !vol_setup(vol, &p, &cube, bmin))
     return TG_EINVAL;
   try {

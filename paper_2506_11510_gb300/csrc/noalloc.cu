@@ -69,7 +69,7 @@ using namespace tv;
 extern "C" int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp,
                                   uint64_t seed, int32_t sample_offset, float* accum_sum, float* accum_sumsq,
                                   void* cuda_stream) {
-  if (!g || !camera_ok(cam) || !medium_ok(med) || spp < 0 || sample_offset < 0 || !accum_sum) return TG_EINVAL;
+  if (!g || !camera_ok(cam) || !medium_ok(med) || !samples_ok(spp, sample_offset) || !accum_sum) return TG_EINVAL;
   const long long npix = (long long)cam->width * cam->height;
   const long long n = npix * spp;
   if (n > NOALLOC_MAX_PATHS) return TG_EINVAL;          // more paths than the scratch array holds
@@ -90,14 +90,9 @@ extern "C" int tet_render_noalloc(const tg_grid* g, const tg_camera* cam, const 
     const unsigned blocks = (unsigned)((n + 255) / 256);
     k_noalloc_paths<<<blocks, 256, 0, st>>>(px, py, ps, n, cam->width, spp, sample_offset);
     TV_LAUNCH();
-    EstParams ep;
-    std::memset(&ep, 0, sizeof ep);
-    ep.cam = camera_setup(*cam, G.box_min, G.cube);
-    ep.med = medium_setup(*med, G.cube);
-    ep.seed = seed;
-    ep.regen_min = TV_REGEN_MIN;
-    ep.ev_min = TV_EV_MIN;
-    for (int a = 0; a < 3; ++a) ep.ext[a] = (float)G.C[a];
+    // the renderer's own parameters for this grid, camera and medium; only the
+    // per-path list, its length, the counter and the output differ
+    EstParams ep = est_params(G, *cam, *med, seed);
     ep.spp = 1;
     ep.total = n;
     ep.counter = counter;

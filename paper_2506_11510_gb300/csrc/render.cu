@@ -217,7 +217,7 @@ void tg_grid_free(tg_grid* g) { delete g; }
 
 int tet_render(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp, uint64_t seed,
                int32_t sample_offset, float* accum_sum, float* accum_sumsq, tg_stats* stats, void* cuda_stream) {
-  if (!g || !camera_ok(cam) || !medium_ok(med) || spp < 0 || sample_offset < 0 || !accum_sum) return TG_EINVAL;
+  if (!g || !camera_ok(cam) || !medium_ok(med) || !samples_ok(spp, sample_offset) || !accum_sum) return TG_EINVAL;
   TV_API_BEGIN
   const GridImpl& G = g->impl;
   cudaStream_t st = (cudaStream_t)cuda_stream;

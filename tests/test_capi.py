@@ -134,3 +134,31 @@ def test_training_bounce_limit_changes_only_the_limit():
     assert RC.with_max_bounces(o, 3).max_bounces == 3 and o.max_bounces == 9
     with pytest.raises(ValueError):
         RC.with_max_bounces(m, 0)
+
+
+def test_sample_ranges_beyond_int32_are_refused_without_a_gpu():
+    """A frame's sample indices [offset, offset + spp) must stay int32: a range past
+    INT32_MAX would wrap and repeat other samples' random streams, so every render
+    entry point refuses it before touching the grid or the device."""
+    import ctypes as C
+    from paper_2506_11510_gb300 import _native as N
+    L = N.lib()
+    cam, med = N.TgCamera(), N.TgMedium()
+    cam.width = cam.height = 8
+    cam.fov_y_deg = 40.0
+    med.max_bounces = 4
+    desc = N.TgVolumeDesc()
+    desc.nx = desc.ny = desc.nz = 8
+    desc.voxel_size = 0.125
+    fake = C.c_void_p(256)              # never dereferenced: the range check comes first
+    ext = N.TgExt()
+    top = (1 << 31) - 1
+    for spp, off in ((2, top - 1), (1, top), (top, 1)):
+        assert L.tet_render(fake, C.byref(cam), C.byref(med), spp, 0, off, fake, None, None, None) == N.TG_EINVAL
+        assert L.tet_render_noalloc(fake, C.byref(cam), C.byref(med), spp, 0, off, fake, None, None) == N.TG_EINVAL
+        assert L.grid_render(fake, C.byref(desc), C.byref(cam), C.byref(med), spp, 0, off, fake, None, None,
+                             None) == N.TG_EINVAL
+        assert L.tet_render_ext(fake, C.byref(cam), C.byref(med), C.byref(ext), spp, 0, off, fake, None, None,
+                                None) == N.TG_EINVAL
+        assert L.tet_render_cached(fake, C.byref(cam), C.byref(med), spp, 0, off, 1, fake, fake, None, None,
+                                   None) == N.TG_EINVAL

@@ -1,14 +1,16 @@
 """tet_render_noalloc, the entry point for callers that may not let a library
 allocate device memory: through the C ABI it gives the same image as
-tet_render (within the render tests' per-pixel tolerance) on two calls in a
-row, the second reusing the static scratch array the first one left behind,
-and it refuses a frame larger than that array."""
+tet_render and as the CPU oracle (within the render tests' per-pixel
+tolerance) on two calls in a row, the second reusing the static scratch array
+the first one left behind; a call after the first changes the device's free
+memory by nothing; and it refuses a frame larger than that array."""
 import ctypes as C
 
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_2506_11510_gb300 import _native as N
 from paper_2506_11510_gb300 import api, workloads as W
 from tests.conftest import scene_volume
@@ -21,20 +23,30 @@ def test_noalloc_render_matches_tet_render_twice():
     vol = torch.from_numpy(scene_volume("tiny")).cuda()
     grid = api.build_scene_grid(s, vol)
     ref, ref2 = api.tet_render(grid, s.camera, s.medium, s.spp, s.render_seed)
+    orc, orc2, _ = O.Grid.for_scene(s, scene_volume("tiny")).render(s.camera, s.medium, s.spp, s.render_seed)
     cam, med = api.camera_struct(s.camera), api.medium_struct(s.medium)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for _ in range(2):
-        out = torch.zeros_like(ref)
-        out2 = torch.zeros_like(ref)
+
+    def close(a, b):
+        return np.mean(np.abs(a - b) <= 1e-4 * np.maximum(np.abs(b), 1e-5) + 1e-6)
+
+    outs = [(torch.zeros_like(ref), torch.zeros_like(ref)) for _ in range(2)]
+    torch.cuda.synchronize()
+    for k, (out, out2) in enumerate(outs):
+        free0 = torch.cuda.mem_get_info()[0]
         st = N.lib().tet_render_noalloc(grid.handle, C.byref(cam), C.byref(med), s.spp, C.c_uint64(s.render_seed),
                                         0, C.c_void_p(out.data_ptr()), C.c_void_p(out2.data_ptr()), stream)
         assert st == N.TG_OK
         torch.cuda.synchronize()
-        g, r = out.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
-        close = np.abs(g - r) <= 1e-4 * np.maximum(np.abs(r), 1e-5) + 1e-6
-        assert close.mean() >= 0.999
-        g2, r2 = out2.cpu().numpy().astype(np.float64), ref2.cpu().numpy().astype(np.float64)
-        assert np.mean(np.abs(g2 - r2) <= 1e-4 * np.maximum(np.abs(r2), 1e-5) + 1e-6) >= 0.999
+        if k > 0:
+            # the entry point's defining property: no device memory is taken by the call
+            assert torch.cuda.mem_get_info()[0] == free0
+        g, g2 = out.cpu().numpy().astype(np.float64), out2.cpu().numpy().astype(np.float64)
+        assert close(g, ref.cpu().numpy().astype(np.float64)) >= 0.999
+        assert close(g2, ref2.cpu().numpy().astype(np.float64)) >= 0.999
+        # and the image is the oracle's (fp64, the same Philox streams)
+        assert close(g, orc) >= 0.999
+        assert close(g2, orc2) >= 0.999
 
 
 def test_noalloc_rejects_frames_beyond_its_scratch():
