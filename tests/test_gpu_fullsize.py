@@ -69,8 +69,16 @@ def test_adaptive_sampled_paths_match_oracle(adaptive):
 
 
 def test_adaptive_full_frame_sampled_pixels(adaptive):
-    """The full 512^2 x 32 spp frame as bench.py renders it; at 64 random pixels the
-    accumulated sums equal the oracle's sums over the same 32 paths."""
+    """The full 512^2 x 32 spp frame as bench.py renders it, at 256 random pixels
+    (8192 paths):
+    * each pixel's accumulated sum is the sum of its 32 paths traced one by one
+      (tet_trace_paths), up to the float additions' rounding: 32 terms added in
+      any order differ by at most 32 * 2^-24 of the sum of their magnitudes;
+    * those paths match the fp64 oracle's (1e-4 relative for >= 99.9%, flags,
+      collision counts, mean difference inside 3 sd / sqrt(n));
+    * so the pixel sums match the oracle's to 1e-4 (floor 1e-6 spp) except where
+      one of their paths is among the <= 0.1% outliers: at least
+      1 - 32 * 0.001 of the pixels, and in practice all."""
     import paper_2506_11510_gb300 as tv
     s, _, _, grid, ref = adaptive
     stats = tv.new_stats()
@@ -78,18 +86,22 @@ def test_adaptive_full_frame_sampled_pixels(adaptive):
     st = tv.stats_dict(stats)
     assert st["paths"] == s.paths_per_frame and st["step_limit"] == 0
     rng = np.random.default_rng(8)
-    pix = rng.integers(0, s.camera.width * s.camera.height, 64)
+    pix = rng.choice(s.camera.width * s.camera.height, 256, replace=False)
     px = np.repeat(pix % s.camera.width, s.spp).astype(np.int32)
     py = np.repeat(pix // s.camera.width, s.spp).astype(np.int32)
     sm = np.tile(np.arange(s.spp), len(pix)).astype(np.int32)
+    got = tv.tet_trace_paths(grid, s.camera, s.medium, s.render_seed, px, py, sm)
     want = ref.render_paths(s.camera, s.medium, s.render_seed, px, py, sm, nthreads=NTHREADS)
-    osum = want["L"].reshape(len(pix), s.spp).sum(1)
-    osq = (want["L"] ** 2).reshape(len(pix), s.spp).sum(1)
+    compare_paths(got, want, seq=False)
+    Lg = got["L"].cpu().numpy().astype(np.float64).reshape(len(pix), s.spp)
     g = img.cpu().numpy().reshape(-1)[pix].astype(np.float64)
     g2 = img2.cpu().numpy().reshape(-1)[pix].astype(np.float64)
-    close = np.abs(g - osum) <= 1e-3 * np.maximum(np.abs(osum), 1e-4)
-    assert close.mean() >= 0.95
-    assert np.allclose(g2, osq, rtol=1e-2, atol=1e-4) or np.mean(np.abs(g2 - osq) <= 1e-2 * np.abs(osq)) >= 0.95
+    bound = s.spp * 2.0 ** -24
+    assert np.all(np.abs(g - Lg.sum(1)) <= bound * np.abs(Lg).sum(1) + 1e-12)
+    assert np.all(np.abs(g2 - (Lg ** 2).sum(1)) <= 2 * bound * (Lg ** 2).sum(1) + 1e-12)
+    osum = want["L"].reshape(len(pix), s.spp).sum(1)
+    close = np.abs(g - osum) <= REL * np.maximum(np.abs(osum), 1e-6 * s.spp)
+    assert close.mean() >= 1 - s.spp * (1 - FRAC)
 
 
 # ---------------------------------------------------------------------------
