@@ -479,7 +479,15 @@ int build_grid(const Volume& V, const Criterion& C, int max_rounds, int nthreads
         for (int p = 0; p < 6; ++p) leaves.push_back(root_tet(D, cx, cy, cz, p));
   std::vector<Stats> st(leaves.size());
   std::vector<char> crit(leaves.size());
-  for (size_t i = 0; i < leaves.size(); ++i) { st[i] = density_stats(V, leaves[i]); crit[i] = split(C, leaves[i], st[i]); }
+  {
+    // one root at a time per thread: each root's statistics scan a whole cube of voxels
+    int nt0 = set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt0)
+    for (int64_t i = 0; i < (int64_t)leaves.size(); ++i) {
+      st[i] = density_stats(V, leaves[i]);
+      crit[i] = split(C, leaves[i], st[i]);
+    }
+  }
   std::unordered_set<uint64_t> verts;
   for (const Tet& t : leaves) for (int i = 0; i < 4; ++i) verts.insert(vkey(t.x[i]));
 
@@ -513,7 +521,9 @@ int build_grid(const Volume& V, const Criterion& C, int max_rounds, int nthreads
       for (int w = 0; w < 2; ++w) { next.push_back(child(leaves[i], w)); nst.push_back(Stats()); ncrit.push_back(2); }
       verts.insert(vkey(next.back().x[leaves[i].tag]));     // z sits at position k of both children
     }
-#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+    // chunks small enough that the few, large cells of the first rounds spread over the threads
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)next.size() / (16 * nt)));
+#pragma omp parallel for schedule(dynamic, chunk) num_threads(nt)
     for (int64_t i = 0; i < (int64_t)next.size(); ++i)
       if (ncrit[i] == 2) { nst[i] = density_stats(V, next[i]); ncrit[i] = split(C, next[i], nst[i]); }
     leaves.swap(next); st.swap(nst); crit.swap(ncrit);
