@@ -865,7 +865,16 @@ struct CacheIO {
   double* query = nullptr;     // [8]: x (3), beta, d (3), L so far; beta = 0 when the path ended before
   int vcap = 0;                // vertices recorded per path
   double* vtx = nullptr;       // [vcap][8]: x (3), target, d (3), valid
+  float survive = 0.0f;        // in (0, 1): Russian roulette once all vcap vertices are recorded
 };
+
+// Russian roulette on a training path after its last training vertex: before
+// each further scattering the path goes on with probability q and its
+// throughput is divided by q, so the expected rest of the path -- and with it
+// every target -- is unchanged, while the path ends after about 1 / (1 - q)
+// more collisions instead of running to the bounce limit.  The decision after
+// collision b is slot b of its own Philox stream, so it shifts no other draw.
+const uint32_t ROULETTE_STREAM = 0x10000u;
 
 // Sec. 3, Algorithm 1 "Trace", with the estimator around it: throughput beta
 // is multiplied by the albedo at every collision; every collision adds the sun
@@ -942,6 +951,11 @@ PathOut trace(const Cells& cells, const Domain& D, const Locate& locate_fn, cons
         q[4] = ray.d.x; q[5] = ray.d.y; q[6] = ray.d.z;
       }
       break;
+    }
+    if (cache && cache->vcap > 0 && nv >= cache->vcap && cache->survive > 0.0f && cache->survive < 1.0f) {
+      const double q = (double)cache->survive;
+      if (uniform(seed, pixel, (uint32_t)sample, (uint32_t)b, ROULETTE_STREAM) >= q) { out.flags |= 32; break; }
+      beta /= q;
     }
     ray.d = sample_phase_function(med->g, uniform(seed, pixel, sample, 3 + 3 * b),
                                   uniform(seed, pixel, sample, 4 + 3 * b), ray.d);   // "SamplePhaseFunction"
@@ -1198,9 +1212,10 @@ int orc_render_paths(const orc_grid* g, const orc_camera* cam, const orc_medium*
 int orc_cache_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* med, uint64_t seed, int64_t n,
                     const int32_t* px, const int32_t* py, const int32_t* sample, int32_t cache_depth,
                     double* query, int32_t max_vertices, double* vertices, double* L, int32_t* flags,
-                    int32_t nthreads) {
+                    float survive, int32_t nthreads) {
   if (!g || !valid_camera(cam) || !valid_medium(med) || n < 0 || cache_depth < 0 || max_vertices < 0 ||
-      max_vertices > 64 || (max_vertices > 0 && !vertices) || (cache_depth > 0 && !query))
+      max_vertices > 64 || (max_vertices > 0 && !vertices) || (cache_depth > 0 && !query) ||
+      !(survive >= 0.0f && survive <= 1.0f))
     return EINVAL_;
   TetCells cells = {g, (double)med->sigma_scale * g->D.cube};
   CamRay cr = camera_rays(cam, g->D);
@@ -1213,6 +1228,7 @@ int orc_cache_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* 
     io.query = cache_depth > 0 ? query + 8 * i : nullptr;
     io.vcap = max_vertices;
     io.vtx = max_vertices > 0 ? vertices + 8 * max_vertices * i : nullptr;
+    io.survive = survive;
     PathOut o = trace(cells, g->D, loc, cr, med, seed, px[i], py[i], sample[i], nullptr, 0, &io);
     if (L) L[i] = o.L;
     if (flags) flags[i] = o.flags;

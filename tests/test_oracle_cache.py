@@ -263,3 +263,63 @@ def test_cache_bernoulli_in_homogeneous_slab():
         w = x - o
         assert np.allclose(np.cross(w, D[i]), 0, atol=1e-9)
         assert np.allclose(q[i, 4:7], D[i], atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Russian roulette on training paths after their last training vertex
+# ---------------------------------------------------------------------------
+def test_roulette_off_is_the_plain_path(tiny_grid):
+    """survive 0 or 1 switches the roulette off: the same vertices, targets and estimates."""
+    s = W.scene("tiny")
+    px, py, sm = all_paths(s.camera, 1)
+    plain = tiny_grid.cache_paths(s.camera, s.medium, 7, px, py, sm, max_vertices=2)
+    for q in (0.0, 1.0):
+        r = tiny_grid.cache_paths(s.camera, s.medium, 7, px, py, sm, max_vertices=2, survive=q)
+        assert np.array_equal(r["vertices"], plain["vertices"]) and np.array_equal(r["L"], plain["L"])
+        assert np.array_equal(r["flags"], plain["flags"])
+
+
+def test_roulette_decision_rate_and_weight():
+    """One roulette per path (bounce limit = training vertices + 1) in a furnace
+    (albedo 1, environment 1, no sun): a path that reaches its last training vertex
+    is ended with probability 1 - q (binomial, 4 sd); a survivor carries throughput
+    1 / q, so it returns exactly 1 / q when it escapes and 0 when the bounce limit
+    truncates it; a path that escapes before the roulette returns exactly 1."""
+    q, J = 0.375, 2
+    vol = np.full((16, 16, 16), 0.5, np.float32)
+    g = O.Grid(vol, (0, 0, 0), 1 / 16, theta=-1, max_depth=6)
+    cam = W.Camera((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0, 1, 0), 40.0, 64, 64)
+    med = W.Medium(1.0, 0.3, 8.0, J + 1, (0, -1, 0), 0.0, 1.0)
+    px, py, sm = all_paths(cam, 16)
+    r = g.cache_paths(cam, med, 9, px, py, sm, max_vertices=J, survive=q)
+    played = r["vertices"][:, J - 1, 7] == 1
+    killed = (r["flags"] & 32) != 0
+    assert np.all(~killed[~played])
+    n, k = int(played.sum()), int(killed.sum())
+    assert n > 5000
+    assert abs(k - n * (1 - q)) <= 4 * math.sqrt(n * q * (1 - q))
+    alive = played & ~killed
+    esc = alive & ((r["flags"] & 2) == 0)
+    assert np.all(r["L"][esc] == 1.0 / q) and np.all(r["L"][alive & ~esc] == 0)
+    assert np.all(r["L"][killed] == 0) and np.all(r["L"][~played & ((r["flags"] & 6) == 0)] == 1)
+
+
+def test_roulette_keeps_the_targets_unbiased(tiny_grid):
+    """The same paths with and without the roulette (q = 1/2 after 2 vertices) on
+    the tiny scene with sun and environment: for every vertex the mean of the
+    target difference is zero within 4 sd / sqrt(n), and the roulette paths are
+    shorter."""
+    s = W.scene("tiny")
+    px, py, sm = all_paths(s.camera, 16)
+    med = W.Medium(0.9, 0.3, 30.0, 64, s.medium.sun_dir, s.medium.sun_irradiance, 0.5)
+    a = tiny_grid.cache_paths(s.camera, med, 13, px, py, sm, max_vertices=2)
+    b = tiny_grid.cache_paths(s.camera, med, 13, px, py, sm, max_vertices=2, survive=0.5)
+    assert np.array_equal(a["vertices"][..., 7], b["vertices"][..., 7])
+    for j in range(2):
+        v = a["vertices"][:, j, 7] == 1
+        d = b["vertices"][v, j, 3] - a["vertices"][v, j, 3]
+        assert v.sum() > 5000 and np.any(d != 0)
+        assert abs(d.mean()) <= 4 * d.std() / math.sqrt(d.size)
+    dL = b["L"] - a["L"]
+    assert abs(dL.mean()) <= 4 * dL.std() / math.sqrt(dL.size)
+    assert ((b["flags"] & 32) != 0).mean() > 0.05
