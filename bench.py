@@ -281,17 +281,25 @@ def run_ours(args):
         out_sq = torch.empty_like(out_sum).pin_memory()
         del grid
         torch.cuda.empty_cache()
-        times = []
+        times, phases = [], None
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.time()
+            ev4 = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            ev4[0].record(st)
             dvol = host_vol.to(dev, non_blocking=True)
+            ev4[1].record(st)
             g2 = tv.build_scene_grid(s, dvol)
+            ev4[2].record(st)
             a, b = tv.tet_render(g2, s.camera, s.medium, spp, s.render_seed, offset)
+            ev4[3].record(st)
             out_sum.copy_(a, non_blocking=True)
             out_sq.copy_(b, non_blocking=True)
+            ev4[4].record(st)
             torch.cuda.synchronize()
             times.append(time.time() - t0)
+            phases = {k: round(ev4[i].elapsed_time(ev4[i + 1]), 2)
+                      for i, k in enumerate(("upload", "build", "render", "download"))}
             del g2, dvol
         e2e_s = sum(times) / len(times)
         if ws > 1:
@@ -301,7 +309,8 @@ def run_ours(args):
         e2e = {"value": round(paths * ws / e2e_s / 1e6, 3), "unit": "Mpaths/s",
                "h2d_bytes_per_step": int(host_vol.numel() * 4), "d2h_bytes_per_step": int(2 * out_sum.numel() * 4),
                "ms_per_step": round(e2e_s * 1e3, 2),
-               "includes": "volume upload, LEB build, frame render, image download"}
+               "includes": "volume upload, LEB build, frame render, image download",
+               "last_step_phases_ms": phases}
 
     peak, peak_kind = load_peaks()
     mean_launch_ms = sum(per_launch) / len(per_launch)
@@ -651,11 +660,11 @@ def cache_leg(args, s, grid, dev, plain_ms):
            "reference_ms": round(ref_ms, 1), "rms_radiance": round(rel, 6),
            "plain": {"spp": s.spp, "ms": round(plain_ms, 2), "rmse": round(target, 6)}, "variants": []}
 
-    def variant(rounds, depth, train_bounces=None, seed_k=0):
+    def variant(rounds, depth, train_bounces=None, seed_k=0, survive=0.0):
         # seed_k selects the initial weights and the training paths (their pixels and random streams)
         rc = RC.RadianceCache(W.mlp_init_params(1 + seed_k, b4=0.1), device=dev, lr=3e-3)
         _, train_ms = timed(lambda: rc.train(grid, s.camera, s.medium, s.render_seed + 7919 * seed_k, rounds=rounds,
-                                             max_bounces=train_bounces))
+                                             max_bounces=train_bounces, survive=survive))
         curve, reached = [], None
         for spp in (1, 2, 4, 8, 16, 32):
             (img, _), ms = timed(lambda: rc.render(grid, s.camera, s.medium, spp, s.render_seed, depth))
@@ -667,24 +676,31 @@ def cache_leg(args, s, grid, dev, plain_ms):
                 "final_train_loss": round(float(rc.loss[2]), 6), "curve": curve,
                 "time_to_equal_rmse_ms": None if reached is None else round(reached, 2)}
 
-    def seeds(rounds, depth, train_bounces=None, n=3):
-        runs = [variant(rounds, depth, train_bounces, k) for k in range(n)]
+    def seeds(rounds, depth, train_bounces=None, n=3, survive=0.0):
+        runs = [variant(rounds, depth, train_bounces, k, survive) for k in range(n)]
         t = [r["time_to_equal_rmse_ms"] for r in runs]
         ok = sorted(x for x in t if x is not None)
         med = statistics.median(t) if len(ok) == len(t) else None
         return {"cache_depth": depth, "train_rounds": rounds, "train_samples_per_round": (1 << 14) * 4,
-                "train_max_bounces": train_bounces or s.medium.max_bounces, "seeds": len(runs),
+                "train_max_bounces": train_bounces or s.medium.max_bounces, "train_survive": survive,
+                "seeds": len(runs),
                 "reached": len(ok), "time_to_equal_rmse_ms_median": None if med is None else round(med, 2),
                 "time_to_equal_rmse_ms_min": ok[0] if ok else None,
                 "time_to_equal_rmse_ms_max": ok[-1] if len(ok) == len(t) else None,
                 "speedup_vs_plain_median": None if med is None else round(plain_ms / med, 3), "runs": runs}
 
-    # the headline: one configuration fixed before this measurement (8 training rounds of
-    # 2^16 vertex samples, paths ending into the cache at their first collision), median of 3 seeds
+    # two configurations fixed before they were measured, each the median of 3 seeds: 8 training
+    # rounds of 2^16 vertex samples, paths ending into the cache at their first collision; the
+    # headline also ends the training paths by Russian roulette (survival 1/2) after their last
+    # training vertex, which leaves every target's expectation unchanged
+    def summary(v):
+        out = {k: val for k, val in v.items() if k != "runs"}
+        out["runs"] = [{k: r[k] for k in ("seed", "train_ms", "time_to_equal_rmse_ms")} for r in v["runs"]]
+        return out
     fixed = seeds(8, 1)
-    res["fixed_configuration"] = {k: v for k, v in fixed.items() if k != "runs"}
-    res["fixed_configuration"]["runs"] = [{k: r[k] for k in ("seed", "train_ms", "time_to_equal_rmse_ms")}
-                                          for r in fixed["runs"]]
+    res["fixed_configuration"] = summary(fixed)
+    fixed_rr = seeds(8, 1, survive=0.5)
+    res["fixed_configuration_roulette"] = summary(fixed_rr)
     # the other training budgets and depths, for context (each the median of 3 seeds as well)
     for rounds in [int(r) for r in str(args.cache_train_rounds).split(",") if r]:
         for depth in (1, 2):
@@ -714,10 +730,11 @@ def cache_leg(args, s, grid, dev, plain_ms):
     _, steps_ms = timed(steps)
     res["train_phases"] = {"trace_paths": n_tr, "trace_ms": round(trace_ms, 2), "steps": 128,
                            "samples_per_step": buf.shape[0] // 128, "steps_ms": round(steps_ms, 2)}
-    med = fixed["time_to_equal_rmse_ms_median"]
+    med = fixed_rr["time_to_equal_rmse_ms_median"]
     res["time_to_equal_rmse_ms"] = med
     res["speedup_vs_plain"] = None if med is None else round(plain_ms / med, 3)
-    res["headline"] = "fixed configuration (8 rounds, cache depth 1), median of 3 training seeds"
+    res["headline"] = ("fixed configuration (8 rounds, cache depth 1, training paths ended by Russian roulette "
+                       "with survival 1/2 after their last training vertex), median of 3 training seeds")
     res["timeouts"] = RC.timeouts()
     return res
 

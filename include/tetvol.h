@@ -367,11 +367,17 @@ int tg_random_paths(uint64_t seed, int64_t n, int32_t width, int32_t height, int
  * the rest of the path's estimate per unit throughput (L_j: the estimate after
  * vertex j's NEE); slots past the path's last collision are all zero.
  * samples: device float[n][max_vertices][8]; L: device float[n] or NULL.
+ * survive in (0, 1): Russian roulette once a path has recorded its max_vertices
+ * samples -- before each further scattering the path goes on with probability
+ * survive (the draw after collision b is slot b of Philox stream 0x10000, counter
+ * (sample, b / 4, 0x10000, 0)) and its throughput is divided by survive, so every
+ * target keeps its expectation while the paths end sooner; 0 or 1: no roulette.
  * Asynchronous.  Shares the grid's scratch counter: serialise with other calls.
+ * TG_EINVAL for survive outside [0, 1].
  */
 int tet_cache_samples(const tg_grid* g, const tg_camera* cam, const tg_medium* med, uint64_t seed, int64_t n,
                       const int32_t* px, const int32_t* py, const int32_t* sample, int32_t max_vertices,
-                      float* samples, float* L, void* cuda_stream);
+                      float* samples, float* L, float survive, void* cuda_stream);
 
 /*
  * tet_cache_queries - the cached estimator's paths for n listed paths: a path

@@ -32,8 +32,9 @@ def random_paths(seed: int, n: int, width: int, height: int, sample_base: int, d
 
 
 def cache_samples(grid: Grid, camera, medium, seed: int, px, py, sample, max_vertices: int, out=None,
-                  want_L: bool = False):
-    """Training samples [n * max_vertices][8] (x, target, d, valid) from full paths."""
+                  want_L: bool = False, survive: float = 0.0):
+    """Training samples [n * max_vertices][8] (x, target, d, valid) from full paths;
+    survive in (0, 1): Russian roulette after a path's last training vertex."""
     px, py, sm, dev = _paths(px, py, sample)
     n = px.numel()
     samples = out if out is not None else torch.empty((n * max_vertices, 8), dtype=torch.float32, device=dev)
@@ -41,7 +42,7 @@ def cache_samples(grid: Grid, camera, medium, seed: int, px, py, sample, max_ver
     L = torch.empty(n, dtype=torch.float32, device=dev) if want_L else None
     N.check(N.lib().tet_cache_samples(grid.handle, C.byref(camera_struct(camera)), C.byref(medium_struct(medium)),
                                       C.c_uint64(seed), n, _ptr(px), _ptr(py), _ptr(sm), int(max_vertices),
-                                      _ptr(samples), _ptr(L), _stream()), "tet_cache_samples")
+                                      _ptr(samples), _ptr(L), float(survive), _stream()), "tet_cache_samples")
     return (samples, L) if want_L else samples
 
 
@@ -140,14 +141,17 @@ class RadianceCache:
 
     def train(self, grid: Grid, camera, medium, seed: int, rounds: int = 1, first_round: int = 0,
               n_paths: int = 1 << 14, max_vertices: int = 4, batches: int = 4, sample_base: int = 1 << 24,
-              max_bounces: Optional[int] = None):
+              max_bounces: Optional[int] = None, survive: float = 0.0):
         """`rounds` training rounds: each traces n_paths full paths at uniform
         pixels (sample indices disjoint from rendering's) and takes `batches`
         Adam steps on their n_paths * max_vertices vertex samples.  The paths
         of all rounds are traced in one launch, then the steps run in order.
         max_bounces, when given, cuts the training paths at that many collisions
         (their targets then miss what lies beyond; the launch no longer waits
-        for the longest paths of the medium's own limit)."""
+        for the longest paths of the medium's own limit).  survive in (0, 1)
+        ends the training paths sooner without biasing them: after their last
+        training vertex they go on with that probability, throughput divided
+        by it (Russian roulette)."""
         if max_bounces is not None:
             medium = with_max_bounces(medium, max_bounces)
         total = rounds * n_paths
@@ -158,7 +162,7 @@ class RadianceCache:
         if self._buf is None or self._buf.shape[0] < nslot:
             self._buf = torch.empty((nslot, 8), dtype=torch.float32, device=self.params.device)
         buf = self._buf[:nslot]
-        cache_samples(grid, camera, medium, seed, px, py, sm, max_vertices, out=buf)
+        cache_samples(grid, camera, medium, seed, px, py, sm, max_vertices, out=buf, survive=survive)
         per_round = n_paths * max_vertices
         per = (per_round + batches - 1) // batches
         for r in range(rounds):

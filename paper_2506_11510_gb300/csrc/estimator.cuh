@@ -12,13 +12,18 @@
 //  * camera rays are formed in fp64 once per path (the eye is far from the
 //    medium, so a direction error becomes a large transverse offset) and kept
 //    as float-float pairs;
-//  * segment origins (collision points) and the optical depth still to
-//    consume are float-float (about 44 bits, on the FP32 pipe);
+//  * segment origins (collision points) are float-float (about 44 bits, on the
+//    FP32 pipe), and the collision point inside its cell is placed in
+//    float-float from the optical depth left;
 //  * the per-segment plane terms P[p] . o are float-float, so exit parameters
 //    carry an error relative to the distance walked, not to |o|.
-// Exit parameters, directions after scattering, densities and shadow walks are
-// fp32: their errors are not amplified.  GB300's FP64 rate is far too low for
-// the per-cell loop; shadow walks are the majority of all cell steps.
+// The optical depth along a segment is summed in fp32 with Kahan compensation
+// (the running sum and the negated low part it lost): per-path parity with the
+// fp64 oracle is the same as with a float-float sum, and the sum is three
+// additions per cell.  Exit parameters, directions after scattering, densities
+// and shadow walks are fp32: their errors are not amplified.  GB300's FP64 rate
+// is far too low for the per-cell loop; shadow walks are the majority of all
+// cell steps.
 //
 // SIMD efficiency.  A warp keeps 32 paths in flight, each in one of four
 // states: idle (waiting for a path id), walking, event (waiting for the warp
@@ -104,6 +109,7 @@ struct EstParams {
   float* cache_rec;                         // [path][8]: x (3), beta, d (3), L so far
   int vtx_cap;                              // trace mode: training samples from the first vtx_cap collisions
   float* vtx;                               // [path][vtx_cap][8]: x (3), target, d (3), valid
+  float survive;                            // in (0, 1): Russian roulette after the last training vertex
   float ext[3];                             // domain extent in grid units (positions are stored over it)
   // extended medium (EXT instantiations): extra per-cell channels, voxel medium
   int ext_flags;                            // 1 emission, 2 per-cell albedo, 4 per-cell g, 8 voxel medium
@@ -143,6 +149,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 enum : int { EXT_EMISSION = 1, EXT_ALBEDO = 2, EXT_G = 4, EXT_VOXEL = 8 };
+// Russian roulette on training paths: the draw after collision b is slot b of this stream.
+constexpr uint32_t ROULETTE_STREAM = 0x10000u;
 // Random numbers of delta / ratio tracking: slot k (the k-th draw of the segment)
 // of stream 1 + 2b (free flight of bounce b) or 2 + 2b (its shadow ray), so that
 // ending one segment early never shifts the draws of another.
@@ -206,7 +214,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
   __shared__ long long job_base[BATCH ? BATCH_MAX_JOBS : 1];
   const Job* job = nullptr;                            // BATCH: the lane's current job
   float sig_l = 0.f;                                   // BATCH: its sigma per unit density (hi word)
-  extern __shared__ double smem_d[];
+  extern __shared__ __align__(16) double smem_d[];
   __shared__ float sun_inv[Walker::NDIR];
   Walker W(wp, smem_d);
   auto med = [&]() -> const MedF& {
@@ -214,6 +222,8 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     else return ep.med;
   };
   const MedF& M0 = ep.med;
+  __shared__ unsigned long long blk_stat[8];           // the block's rarer frame counters (see below)
+  if (threadIdx.x < 8) blk_stat[threadIdx.x] = 0ull;
   if (BATCH) {
     for (int i = threadIdx.x; i < ep.njobs; i += blockDim.x) job_base[i] = jobs[i].base;
     if (threadIdx.x == 0) atomicMin(ep.job_time + ep.njobs, global_ns());
@@ -246,7 +256,13 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
   float Tr = 1.f;                                      // EXT: ratio-tracking transmittance
   ff3 os = {ff_make(0.f), ff_make(0.f), ff_make(0.f)}; // EXT: shadow segment origin (voxel medium)
   long long psteps = 0;
-  uint32_t c_paths = 0, c_steps = 0, c_shadow = 0, c_coll = 0, c_esc = 0, c_trunc = 0, c_lim = 0, c_miss = 0;
+  // the frame's counters: cell steps in registers (added at every segment end), the
+  // rarer ones -- paths, collisions, escapes, truncations, step limits, misses -- in
+  // one shared set per block, so that they hold no registers through the cell loop
+  uint32_t c_steps = 0, c_shadow = 0;
+  auto bump = [&](int i) {
+    if (ep.stats) atomicAdd(&blk_stat[i], 1ull);
+  };
 
   auto record = [&](int v) {
     if (TRACE) {
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     }
   };
   auto finish = [&]() {
-    ++c_paths;
+    bump(0);
     const float Lf = ff_float(L);
     if (TRACE) {
       if (ep.outL) ep.outL[pid] = Lf;
@@ -399,7 +415,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           const float3 eye = make_float3((float)c.eye[0], (float)c.eye[1], (float)c.eye[2]);
           float tin;
           if (!W.intersect(eye, dir, &tin)) {
-            L = ff_make(M.Lenv); flags = 4; ++c_miss; ++c_esc;
+            L = ff_make(M.Lenv); flags = 4; bump(7); bump(4);
             finish();
           } else {
             // the entry point: any error along the ray is harmless (no medium outside the box)
@@ -456,7 +472,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
             } else {
               beta *= M.albedo;
             }
-            ++ncoll; ++c_coll;
+            ++ncoll; bump(3);
             record(-1);
             saved = W.save();
             W.begin(o, sun_tab);
@@ -475,7 +491,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
             state = S_WALK;
           }
         } else {
-          L = ff_add(L, ff_make(beta * M.Lenv)); ++c_esc;
+          L = ff_add(L, ff_make(beta * M.Lenv)); bump(4);
           finish();
         }
       } else if (voxel && ev == EV_LIMIT) {
@@ -511,7 +527,7 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           ++nv;
         }
         if (bounce + 1 >= M.max_bounces) {
-          flags |= 2; ++c_trunc;
+          flags |= 2; bump(5);
           finish();
         } else if (MODE != MODE_RENDER && ep.cache_depth > 0 && bounce + 1 == ep.cache_depth) {
           // the path ends into the radiance cache, which stands for the rest of it
@@ -520,7 +536,15 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           r[1] = make_float4(d.x.hi, d.y.hi, d.z.hi, ff_float(L));
           queried = true;
           finish();
+        } else if (TRACE && ep.vtx && nv >= ep.vtx_cap && ep.survive > 0.f && ep.survive < 1.f &&
+                   rng_u(seedv(), pixel, sample, (uint32_t)bounce, ROULETTE_STREAM) >= ep.survive) {
+          // a training path past its last training vertex ends by Russian roulette
+          flags |= 32;
+          finish();
         } else {
+          // (a training path that survives the roulette carries throughput / survive)
+          if (TRACE && ep.vtx && nv >= ep.vtx_cap && ep.survive > 0.f && ep.survive < 1.f)
+            beta = __fdiv_rn(beta, ep.survive);
           // SamplePhaseFunction, then a new free flight from the collision point
           const float3 nd = hg_scatter(gg, rng_u(seedv(), pixel, sample, 3 + 3 * bounce),
                                        rng_u(seedv(), pixel, sample, 4 + 3 * bounce),
@@ -544,23 +568,29 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
       if (!h.ok) { count_steps(seg_steps - 1); flags |= 16; finish(); break; }
       // the voxel medium walks the cells' majorants
       const float rho = voxel ? __ldg(ep.vmaj + W.cell()) : h.rho;
-      // optical depth of the cell: (sigma_unit * rho) * (t_exit - t), the product kept exactly
-      const ff sig = two_prod(BATCH ? sig_l : M0.sig_hi, rho);
-      const ff dtau = ff_mul_f(sig, h.texit - t);
-      const ff sum = ff_add_fast(acc, dtau);
-      // (the limit is a float: comparing the high word decides all but exact ties, which
+      // optical depth of the cell, (sigma_unit * rho) * (t_exit - t), added to the segment's
+      // sum with Kahan compensation: acc.hi is the running sum, acc.lo the negated low part
+      // it lost (the sum is acc.hi - acc.lo)
+      const float sigf = BATCH ? sig_l : M0.sig_hi;
+      const float y = (sigf * rho) * (h.texit - t) - acc.lo;
+      const float sum = acc.hi + y;
+      // (the limit is a float: comparing the rounded sum decides all but exact ties, which
       // only move a collision by less than one unit in the last place of the free path)
-      if (rho > 0.f && !(sum.hi < lim)) {
-        // the segment's optical-depth limit falls inside this cell
+      if (rho > 0.f && !(sum < lim)) {
+        // the segment's optical-depth limit falls inside this cell: place it in float-float
+        const ff sig = two_prod(sigf, rho);
+        acc = ff{acc.hi, -acc.lo};
         if (mode == M_FREE || voxel) acc = ff_add(ff_make(t), ff_div(ff_sub(ff_make(lim), acc), sig));
         count_steps(seg_steps);
         ev = EV_LIMIT;
         state = S_EVENT;
         break;
       }
-      acc = sum;
+      acc.lo = (sum - acc.hi) - y;
+      acc.hi = sum;
       t = h.texit;
       if (!W.advance()) {
+        acc = ff{acc.hi, -acc.lo};          // the segment's optical depth as a float-float value
         count_steps(seg_steps);
         ev = EV_BOUNDARY;
         state = S_EVENT;
@@ -569,21 +599,21 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
     // a segment that walks too many cells (a corrupt grid) ends its path
     if (state == S_WALK && seg_steps >= SEG_STEP_LIMIT) {
       count_steps(seg_steps);
-      flags |= 8; ++c_lim;
+      flags |= 8; bump(6);
       finish();
     }
   }
 
   if (ep.stats) {
-    const unsigned long long v[8] = {warp_sum(c_paths), warp_sum(c_steps), warp_sum(c_shadow), warp_sum(c_coll),
-                                     warp_sum(c_esc), warp_sum(c_trunc), warp_sum(c_lim), warp_sum(c_miss)};
+    const unsigned long long ws = warp_sum(c_steps), wsh = warp_sum(c_shadow);
     if (lane == 0) {
-      unsigned long long* s = reinterpret_cast<unsigned long long*>(ep.stats);
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (v[i]) atomicAdd(s + i, v[i]);
+      atomicAdd(&blk_stat[1], ws);
+      atomicAdd(&blk_stat[2], wsh);
     }
   }
+  __syncthreads();
+  if (ep.stats && threadIdx.x < 8 && blk_stat[threadIdx.x])
+    atomicAdd(reinterpret_cast<unsigned long long*>(ep.stats) + threadIdx.x, blk_stat[threadIdx.x]);
 }
 
 // Launch the persistent estimator: as many resident blocks as fit, one wave.

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(EST_BLOCK) k_optical_depth(const TetParams P, 
                                                             const float* dir, float sigma, float* tau,
                                                             int64_t* steps, int32_t* seq, int seq_cap,
                                                             int32_t* seq_len) {
-  extern __shared__ double smem_d[];
+  extern __shared__ __align__(16) double smem_d[];
   TetWalker<FMT> W(P, smem_d);
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;

@@ -4,15 +4,20 @@
 // ray moves to the neighbour across it.
 //
 // Face planes only take the 9 orientations P = {x, y, z, x+y, x-y, y+z, y-z,
-// x+z, x-z}, so per segment the walker keeps, for each orientation p,
-// nO[p] = (P[p] . o) 2^K and invND[p] = 2^-K / (P[p] . d) in shared memory
-// (one column per thread: conflict-free), and the exit parameter of a face with
-// integer plane offset c (units of 2^-K) is (c - nO[p]) * invND[p].  The
-// reciprocals are stored per orientation id p | s << 4, NaN where the outward
-// normal does not point along d (a face that cannot be an exit).
-// Free flights keep nO as a float-float pair (hi, lo), so that c - nO is
-// accurate to the distance walked rather than to |o|; shadow walks keep it as
-// one float.  Both use the same per-thread 8-byte slots.
+// x+z, x-z}, so per segment the walker keeps, for each orientation p, one
+// 16-byte entry in shared memory (one column per thread: conflict-free):
+// nO[p] = (P[p] . o) 2^K as a float-float pair (hi, lo), and 2^-K / (P[p] . d)
+// for the outward normals +P[p] and -P[p] -- NaN for the one that does not point
+// along d (a face that cannot be an exit).  The exit parameter of a face with
+// integer plane offset c (units of 2^-K) is then (c - nO.hi - nO.lo) times the
+// reciprocal of its normal's sign: one 16-byte load per face.  The float-float
+// nO keeps c - nO accurate to the distance walked rather than to |o|.
+//
+// The walk is a chain of dependent record loads.  To shorten each link the
+// walker loads the record of the cell it moves to as soon as the exit face is
+// known -- before the caller's optical-depth work and before any warp-wide
+// event round -- into the same registers that held the current record.  A
+// segment start (begin) loads the record of the cell it starts in.
 #pragma once
 #include "estimator.cuh"
 
@@ -158,40 +163,24 @@ __device__ __forceinline__ void tet_dir_table(const ff3& d, float invK, float in
   }
 }
 
-#ifndef TV_LD256
-#define TV_LD256 0                      // fetch a 32-byte record with one 256-bit load
-#endif
-
-#ifndef TV_PREFETCH
-#define TV_PREFETCH 0                   // load the next cell's record as soon as the exit face is known
-#endif
-
 // BATCH: the walker of a batch of grids -- the grid (and so its parameters)
 // changes from path to path and from lane to lane; set_job points it at one.
 template <int FMT, bool BATCH = false>
 struct TetWalker {
   using Params = TetParams;
-  static constexpr int NDIR = TET_NID;      // direction-table entries
+  static constexpr int NDIR = TET_NID;      // direction-table entries (tet_dir_table's layout)
   const TetParams& P0;                      // the grid's parameters (uniform)
   const TetParams* Pj = nullptr;            // BATCH: the current path's grid
   const uint4* brec = nullptr;              // BATCH: its records
-  double* tab;         // this thread's column: nO pair p at tab[p * EST_BLOCK] (9 slots), then the
-                       // direction table as floats, entry q at ((float*)(tab0 + 9 EST_BLOCK))[q * EST_BLOCK]
-  float* itab;
+  float4* tab;         // the block's segment table; entry p of this thread at tab[p * EST_BLOCK + threadIdx.x]
   int cur, nxt;
-#if TV_PREFETCH
-  uint4 ra, rb;        // record of the current cell
-  uint4 na, nb;        // record of the pending next cell, in flight
-#endif
+  uint4 ra, rb;        // the record of the cell the walk is in (loaded ahead, see above)
 
-  static size_t smem_bytes() { return (sizeof(double) * 9 + sizeof(float) * TET_NID) * EST_BLOCK; }
+  static size_t smem_bytes() { return sizeof(float4) * 9 * EST_BLOCK; }
 
   __device__ TetWalker(const TetParams& p, double* smem)
-      : P0(p), tab(smem + threadIdx.x), itab(reinterpret_cast<float*>(smem + 9 * EST_BLOCK) + threadIdx.x), cur(0),
-        nxt(0) {
-#if TV_PREFETCH
-    ra = rb = na = nb = make_uint4(NO_NBR, NO_NBR, NO_NBR, NO_NBR);
-#endif
+      : P0(p), tab(reinterpret_cast<float4*>(smem)), cur(0), nxt(0) {
+    ra = rb = make_uint4(NO_NBR, NO_NBR, NO_NBR, NO_NBR);
   }
 
   __device__ __forceinline__ const TetParams& prm() const {
@@ -207,8 +196,9 @@ struct TetWalker {
     brec = p->rec;
   }
 
-  __device__ __forceinline__ float2& pair(int q) { return *reinterpret_cast<float2*>(tab + q * EST_BLOCK); }
-  __device__ __forceinline__ float2 pair(int q) const { return *reinterpret_cast<const float2*>(tab + q * EST_BLOCK); }
+  // (the address is formed from the block's base and threadIdx.x each time: no per-thread
+  // pointer stays live through the cell loop)
+  __device__ __forceinline__ float4& entry(int p) { return tab[p * EST_BLOCK + threadIdx.x]; }
 
   __device__ bool intersect(float3 o, float3 d, float* t_in) const { return box_intersect(prm().C, o, d, t_in); }
 
@@ -238,9 +228,6 @@ struct TetWalker {
         const float len = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
         cur = start;
         c = start;
-#if TV_PREFETCH
-        load(ra, rb);        // the walk below reads the current cell's record from ra, rb
-#endif
         if (len > 0.f) {
           const float inv = 1.0f / len;
           float tinv[TET_NID];
@@ -258,93 +245,69 @@ struct TetWalker {
       }
     }
     if (c < 0) c = tet_locate(P, p);
-    cur = (int)c;
-#if TV_PREFETCH
-    if (c >= 0) load(ra, rb);
-#endif
+    cur = (int)c;                  // the segment that starts here loads its record (begin)
     return c >= 0;
   }
 
   __device__ __forceinline__ void dir_table(const ff3& d, float inv[TET_NID]) const { tet_dir_table(d, prm().invK, inv); }
 
-  // Per-segment table: nO[p] = (P[p] . o) 2^K as a float-float pair (so c - nO is
-  // accurate to the distance walked, not to |o|), and the direction table.
+  // the 32-byte record of cell i (one DRAM sector) with one 256-bit load
+  __device__ __forceinline__ void load(int i, uint4& a, uint4& b) const {
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(recs() + 2 * (size_t)i));
+  }
+
+  // Per-segment table for the ray o + t d (direction table inv from dir_table):
+  // nO[p] as a float-float pair and the two reciprocals of normal p; then the
+  // record of the current cell, where the segment starts.
   __device__ void begin(const ff3& o, const float* inv) {
     const ff no[9] = {o.x, o.y, o.z, ff_add(o.x, o.y), ff_sub(o.x, o.y), ff_add(o.y, o.z), ff_sub(o.y, o.z),
                       ff_add(o.x, o.z), ff_sub(o.x, o.z)};
     const float scaleK = prm().scaleK;
 #pragma unroll
-    for (int p = 0; p < 9; ++p) pair(p) = make_float2(no[p].hi * scaleK, no[p].lo * scaleK);
-#pragma unroll
-    for (int q = 0; q < TET_NID; ++q) itab[q * EST_BLOCK] = inv[q];
-  }
-
-  __device__ __forceinline__ void load(uint4& a, uint4& b) const {
-#if TV_LD256
-    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
-                 : "l"(recs() + 2 * (size_t)cur));
-#else
-    a = __ldg(recs() + 2 * (size_t)cur);
-    b = __ldg(recs() + 2 * (size_t)cur + 1);
-#endif
+    for (int p = 0; p < 9; ++p) entry(p) = make_float4(no[p].hi * scaleK, no[p].lo * scaleK, inv[p], inv[p | 16]);
+    load(cur, ra, rb);
   }
 
   // Exit of the current cell from parameter t.  All four faces are evaluated; the
   // ones whose outward normal does not face the ray get a NaN parameter from the
-  // direction table and never win, so the lanes of a warp run one instruction stream.
+  // table and never win, so the lanes of a warp run one instruction stream.  The
+  // record of the exit neighbour is requested before returning.
   __device__ __forceinline__ Hop hop(float t) {
-#if TV_PREFETCH
     const uint4 a = ra, b = rb;
-#else
-    uint4 a, b;
-    load(a, b);
-#endif
     const uint32_t link[4] = {a.x, a.y, a.z, a.w};
     // the four planes: bytes 0-2, 3-5, 6-8 and 9-11 of (b.x, b.y, b.z), sign-extended
     const int c[4] = {prmt_s24(b.x, b.y, 0xA210u), prmt_s24(b.x, b.y, 0xD543u), prmt_s24(b.y, b.z, 0xC432u),
                       prmt_s24(b.z, 0u, 0xB321u)};
+    const float rho = decode_density<FMT>(b.w);
     float best = INFINITY;
     uint32_t blink = NO_NBR;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      const uint32_t id = link[f] >> 27;
-      const float2 no = pair((int)(id & 15u));
-      const float tf = __fmul_rn(__fsub_rn(__fsub_rn((float)c[f], no.x), no.y), itab[id * EST_BLOCK]);
+      // orientation id p | s << 4 in the link's top five bits: p selects the entry, s (bit 31) the sign
+      const float4 e = entry((int)((link[f] >> 27) & 15u));
+      const float tf = __fmul_rn(__fsub_rn(__fsub_rn((float)c[f], e.x), e.y), (int)link[f] < 0 ? e.w : e.z);
       const bool better = tf < best;
       best = better ? tf : best;
       blink = better ? link[f] : blink;
     }
     nxt = (int)(blink & NO_NBR);
-#if TV_PREFETCH
-    if ((uint32_t)nxt != NO_NBR) {
-      na = __ldg(recs() + 2 * (size_t)nxt);
-      nb = __ldg(recs() + 2 * (size_t)nxt + 1);
-    }
-#endif
+    if ((uint32_t)nxt != NO_NBR) load(nxt, ra, rb);
     Hop h;
     h.ok = best < INFINITY;
     h.texit = fmaxf(best, t);
-    h.rho = decode_density<FMT>(b.w);
+    h.rho = rho;
     return h;
   }
 
   __device__ __forceinline__ bool advance() {
     if ((uint32_t)nxt == NO_NBR) return false;
-    cur = nxt;
-#if TV_PREFETCH
-    ra = na;
-    rb = nb;
-#endif
+    cur = nxt;                     // its record is already in ra, rb
     return true;
   }
   __device__ __forceinline__ int save() const { return cur; }
-  __device__ __forceinline__ void restore(int c) {
-    cur = c;
-#if TV_PREFETCH
-    load(ra, rb);
-#endif
-  }
+  __device__ __forceinline__ void restore(int c) { cur = c; }   // the next begin loads its record
   __device__ __forceinline__ int cell() const { return cur; }
 };
 

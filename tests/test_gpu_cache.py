@@ -147,16 +147,19 @@ def _paths(s, n, seed):
             g.integers(0, 64, n).astype(np.int32))
 
 
-def test_cache_samples_match_oracle(scene_pair):
+@pytest.mark.parametrize("survive", [0.0, 0.5])
+def test_cache_samples_match_oracle(scene_pair, survive):
     """Vertex training samples: positions, arrival directions, targets (the rest
-    of the path per unit throughput) and validity per path and vertex."""
+    of the path per unit throughput) and validity per path and vertex; with
+    survive = 0.5 the training paths end by Russian roulette after their last
+    training vertex, with the oracle's decisions."""
     from paper_2506_11510_gb300 import cache as RC
     s, grid, ref = scene_pair
     px, py, sm = _paths(s, 4000, 3)
-    J = 4
-    got, L = RC.cache_samples(grid, s.camera, s.medium, s.render_seed, px, py, sm, J, want_L=True)
+    J = 4 if survive == 0 else 2
+    got, L = RC.cache_samples(grid, s.camera, s.medium, s.render_seed, px, py, sm, J, want_L=True, survive=survive)
     got = got.cpu().numpy().astype(np.float64).reshape(-1, J, 8)
-    want = ref.cache_paths(s.camera, s.medium, s.render_seed, px, py, sm, max_vertices=J)
+    want = ref.cache_paths(s.camera, s.medium, s.render_seed, px, py, sm, max_vertices=J, survive=survive)
     wv = want["vertices"]
     same_valid = np.all(got[..., 7] == wv[..., 7], axis=1)
     pos = np.all(np.abs(got[..., 0:3] - wv[..., 0:3]) <= 1e-4, axis=(1, 2))
@@ -164,7 +167,9 @@ def test_cache_samples_match_oracle(scene_pair):
     tg = np.all(np.abs(got[..., 3] - wv[..., 3]) <= 1e-4 * np.maximum(np.abs(wv[..., 3]), 1e-3), axis=1)
     ok = same_valid & pos & drc & tg
     assert ok.mean() >= 0.999, (same_valid.mean(), pos.mean(), drc.mean(), tg.mean())
-    assert wv[..., 7].sum() > 2000
+    assert wv[..., 7].sum() > (2000 if survive == 0 else 1000)
+    if survive > 0:
+        assert ((want["flags"] & 32) != 0).mean() > 0.05        # the roulette ends paths
     Lo = want["L"]
     assert np.mean(np.abs(L.cpu().numpy() - Lo) <= 1e-4 * np.maximum(np.abs(Lo), 1e-6)) >= 0.999
 
