@@ -117,8 +117,11 @@ int leb_rebuild(const tg_grid* prev, const float* density, const tg_volume_desc*
                 float target_footprint_px, float variation_threshold, int32_t max_depth, int32_t density_format,
                 void* cuda_stream, tg_grid** out);
 
-/* Size and shape of a grid.  Any output pointer may be NULL.  bytes: device bytes
- * the renderer reads (records + codes); K: vertex coordinate scale exponent. */
+/* tg_grid_info - size and shape of a grid built by leb_build (Sec. 2): the
+ * number of leaves (tetrahedra), the deepest LEB level present, the build's
+ * rounds of bisection.  Any output pointer may be NULL.  bytes: device bytes the
+ * renderer reads (records + codes); K: vertex coordinate scale exponent.
+ * Host-only (no CUDA call).  TG_EINVAL for a NULL grid. */
 int tg_grid_info(const tg_grid* g, int64_t* num_tets, int32_t* max_depth, int64_t* bytes,
                  int32_t* K, int32_t* rounds);
 
@@ -151,6 +154,9 @@ int tg_grid_import(const tg_volume_desc* vol, int32_t K, int64_t num_tets, const
                    const int32_t* nbr, const uint8_t* nid, const float* plane, const float* density,
                    int32_t density_format, void* cuda_stream, tg_grid** out);
 
+/* tg_grid_free - release a grid and every device buffer it owns.  The paper has
+ * no counterpart (resource management of this library).  NULL is ignored; the
+ * grid must not be in use by work still queued on any stream. */
 void tg_grid_free(tg_grid* g);
 
 /*
@@ -438,6 +444,9 @@ int tet_render_cached(const tg_grid* g, const tg_camera* cam, const tg_medium* m
  * library was loaded (0 in a healthy run).  Synchronises the device. */
 int rc_timeouts(int64_t* count);
 
+/* tg_error_string - a static, human-readable name for a status code (TG_OK and
+ * the TG_E* codes; "unknown status" otherwise).  The paper has no counterpart.
+ * Never fails; needs no GPU. */
 const char* tg_error_string(int status);
 
 #ifdef __cplusplus
