@@ -90,7 +90,11 @@ typedef struct tg_grid tg_grid;    /* device-resident grid, owned by the library
  * (the voxel of its centroid when there are none); and every leaf holding a
  * vertex at one of its edge midpoints is bisected too, until no leaf is
  * selected (the conformity-preserving propagation of Sec. 2).
- *   density  device float[nz][ny][nx]; read during the call only.
+ *   density  float[nz][ny][nx]: device memory, or page-locked (pinned) host
+ *            memory that the device addresses directly -- the build reads each
+ *            value once, in its quantisation kernel, so a pinned host volume
+ *            needs no separate upload.  Pageable host memory is refused with
+ *            TG_EINVAL before any kernel runs.  Read during the call only.
  *   cam      host struct, or NULL to switch the camera criterion off (as does
  *            target_footprint_px <= 0); variation_threshold < 0 switches
  *            criterion 1 off.
@@ -411,8 +415,9 @@ int rc_mlp_infer(const float* params, const float* rec, int64_t n, float* y, voi
  * training samples and its gradient: grad (device float[RC_NUM_PARAMS]) += the
  * gradient of that sum (not divided by the count); loss (device float[3]):
  * loss[0] += the sum, loss[1] += sum_i valid_i.  One fused forward + backward
- * kernel; weight gradients accumulate in tensor memory across a block's tiles.
- * Asynchronous.
+ * kernel; weight gradients accumulate in tensor memory across a block's tiles
+ * and each block adds its sums into grad with 16-byte atomics, so grad must be
+ * 16-byte aligned (TG_EINVAL otherwise).  Asynchronous.
  */
 int rc_mlp_grad(const float* params, const float* samples, int64_t n, float* grad, float* loss, void* cuda_stream);
 

@@ -146,10 +146,23 @@ def ext_struct(flags: int, emission_scale: float = 0.0, density: Optional[torch.
     return x
 
 
+def _need_volume(t: torch.Tensor, name: str = "density"):
+    """A volume a build reads once: a CUDA tensor, or a pinned (page-locked) host
+    tensor that the device reads in place."""
+    if isinstance(t, torch.Tensor) and not t.is_cuda and t.is_pinned():
+        if t.dtype != torch.float32:
+            raise TypeError("%s must be float32, got %s" % (name, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        return t
+    return _need(t, torch.float32, name)
+
+
 def leb_build(density: torch.Tensor, box_min, voxel_size, camera=None, footprint_px: float = 0.0,
               variation_threshold: float = -1.0, max_depth: int = 12, density_format: int = 0) -> Grid:
-    """Sec. 2: build the adaptive conforming LEB grid of a density volume float32[nz][ny][nx]."""
-    _need(density, torch.float32, "density")
+    """Sec. 2: build the adaptive conforming LEB grid of a density volume float32[nz][ny][nx]
+    (a CUDA tensor, or a pinned host tensor that the build reads in place)."""
+    _need_volume(density)
     if density.dim() != 3:
         raise ValueError("density must be [nz, ny, nx]")
     desc = volume_desc(density, box_min, voxel_size)
@@ -163,7 +176,7 @@ def leb_build(density: torch.Tensor, box_min, voxel_size, camera=None, footprint
 def leb_rebuild(prev: Grid, density: torch.Tensor, box_min, voxel_size, camera=None, footprint_px: float = 0.0,
                 variation_threshold: float = -1.0, max_depth: int = 12, density_format: int = 0) -> Grid:
     """leb_build for a new camera on the volume `prev` was built from, reusing its node statistics."""
-    _need(density, torch.float32, "density")
+    _need_volume(density)
     desc = volume_desc(density, box_min, voxel_size)
     cam = C.byref(camera_struct(camera)) if camera is not None else None
     h = C.c_void_p()

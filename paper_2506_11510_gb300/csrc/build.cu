@@ -189,15 +189,31 @@ __device__ __forceinline__ int p9_dot(int p, const int v[3]) {
 // ---------------------------------------------------------------------------
 // A1: quantise density to q = round(rho 2^24) in [0, 2^24]
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t quantize1(float rho) {
+  const float v = rho * 16777216.0f;
+  if (!(v > 0.0f)) return 0u;
+  if (v >= 16777216.0f) return 16777216u;
+  return (uint32_t)rintf(v);
+}
+
+// rho may be device memory or page-locked host memory the device addresses
+// directly (then each element crosses the host link exactly once, here): 16-byte
+// loads when the volume is 16-byte aligned, one element at a time otherwise.
 __global__ void k_quantize(const float* __restrict__ rho, uint32_t* __restrict__ q, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float v = rho[i] * 16777216.0f;
-    uint32_t r;
-    if (!(v > 0.0f)) r = 0;
-    else if (v >= 16777216.0f) r = 16777216u;
-    else r = (uint32_t)rintf(v);
-    q[i] = r;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long done = 0;
+  if ((reinterpret_cast<uintptr_t>(rho) & 15u) == 0 && (reinterpret_cast<uintptr_t>(q) & 15u) == 0) {
+    const long long n4 = n / 4;
+    const float4* r4 = reinterpret_cast<const float4*>(rho);
+    uint4* q4 = reinterpret_cast<uint4*>(q);
+    for (long long i = i0; i < n4; i += stride) {
+      const float4 v = r4[i];
+      q4[i] = make_uint4(quantize1(v.x), quantize1(v.y), quantize1(v.z), quantize1(v.w));
+    }
+    done = 4 * n4;
   }
+  for (long long i = done + i0; i < n; i += stride) q[i] = quantize1(rho[i]);
 }
 
 // A2: six Kuhn tetrahedra per cube, tag 3, in root-id order
@@ -1243,6 +1259,20 @@ extern "C" int tg_grid_export_channels(const tg_grid* g, float* chan, float* vma
   return TG_OK;
 }
 
+// The volume a build reads: device memory, or page-locked (pinned) host memory
+// that the device addresses directly -- read once, by the quantisation kernel.
+// Pageable host memory is refused before any kernel could touch it.
+static int build_volume_pointer(const float* p, const float** dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return TG_ECUDA;
+  }
+  if (a.type == cudaMemoryTypeUnregistered) return TG_EINVAL;
+  *dev = a.devicePointer ? static_cast<const float*>(a.devicePointer) : p;
+  return TG_OK;
+}
+
 extern "C" int leb_build(const float* density, const tg_volume_desc* vol, const tg_camera* cam,
                          float target_footprint_px, float variation_threshold, int32_t max_depth,
                          int32_t density_format, void* cuda_stream, tg_grid** out) {
@@ -1251,6 +1281,8 @@ extern "C" int leb_build(const float* density, const tg_volume_desc* vol, const 
     return TG_EINVAL;
   if ((long long)vol->nx * vol->ny * vol->nz >= (1ll << 34)) return TG_EINVAL;
   if (cam && !tv::camera_ok(cam)) return TG_EINVAL;
+  const int vs = build_volume_pointer(density, &density);
+  if (vs != TG_OK) return vs;
   tg_grid* g = new (std::nothrow) tg_grid();
   if (!g) return TG_ENOMEM;
   int st;
@@ -1278,6 +1310,8 @@ extern "C" int leb_rebuild(const tg_grid* prev, const float* density, const tg_v
     return TG_EINVAL;
   if ((long long)vol->nx * vol->ny * vol->nz >= (1ll << 34)) return TG_EINVAL;
   if (cam && !tv::camera_ok(cam)) return TG_EINVAL;
+  const int vs = build_volume_pointer(density, &density);
+  if (vs != TG_OK) return vs;
   tg_grid* g = new (std::nothrow) tg_grid();
   if (!g) return TG_ENOMEM;
   int st;

@@ -94,3 +94,39 @@ def test_build_rejects_bad_arguments():
     with pytest.raises(tv.TetvolError):
         # 9 x 8 x 8 cubes of 2^3 voxels -> 3456 roots, more than the code's 8 root bits
         tv.leb_build(torch.zeros((16, 16, 18), device="cuda"), (0, 0, 0), 1 / 16, max_depth=3)
+
+
+@pytest.mark.parametrize("name", ["adaptive_small", "production_small"])
+def test_build_from_pinned_host_volume(name):
+    """leb_build reads a pinned host volume in place (each value once, in the
+    quantisation kernel): the grid equals the build from the same volume in
+    device memory, bit for bit, and a rebuild from it equals one from device memory."""
+    import paper_2506_11510_gb300 as tv
+    s = W.scene(name)
+    host = torch.from_numpy(scene_volume(name)).pin_memory()
+    dev = host.cuda()
+    a = gpu_arrays(tv.build_scene_grid(s, dev))
+    g = tv.build_scene_grid(s, host)
+    b = gpu_arrays(g)
+    for k in FIELDS:
+        assert np.array_equal(a[k], b[k]), k
+    s1 = W.with_camera(s, pos=(s.camera.pos[0] + 0.2, s.camera.pos[1], s.camera.pos[2]))
+    r1 = gpu_arrays(tv.rebuild_scene_grid(g, s1, host))
+    r2 = gpu_arrays(tv.build_scene_grid(s1, dev))
+    for k in ("codes", "nbr", "density"):
+        assert np.array_equal(r1[k], r2[k]), k
+
+
+def test_build_refuses_pageable_host_memory():
+    """A pageable host volume is refused before any kernel runs (the device could not read it)."""
+    import ctypes as C
+    from paper_2506_11510_gb300 import _native as N
+    from paper_2506_11510_gb300 import api
+    s = W.scene("tiny")
+    vol = np.ascontiguousarray(scene_volume("tiny"))          # ordinary (pageable) host memory
+    desc = api.volume_desc(torch.from_numpy(vol), s.box_min, s.voxel_size)
+    out = C.c_void_p()
+    st = N.lib().leb_build(C.c_void_p(vol.ctypes.data), C.byref(desc), None, 0.0, -1.0, 6, 0, None, C.byref(out))
+    assert st == N.TG_EINVAL and not out.value
+    with pytest.raises(TypeError):
+        api.leb_build(torch.from_numpy(vol), s.box_min, s.voxel_size)
