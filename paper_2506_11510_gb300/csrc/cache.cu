@@ -30,6 +30,7 @@ constexpr int WID = 64, ENC = 128, PFREQ = 12, DFREQ = 4;
 constexpr int O_W1 = 0, O_B1 = O_W1 + WID * ENC, O_W2 = O_B1 + WID, O_B2 = O_W2 + WID * WID, O_W3 = O_B2 + WID,
               O_B3 = O_W3 + WID * WID, O_W4 = O_B3 + WID, O_B4 = O_W4 + WID, NPARAM = O_B4 + 1;
 static_assert(NPARAM == RC_NUM_PARAMS, "parameter layout");
+static_assert(O_W1 % 4 == 0 && O_W2 % 4 == 0 && O_W3 % 4 == 0, "weight blocks start on 16-byte boundaries");
 constexpr int MT = 128;                      // rows per tile (MMA M) = threads per block
 constexpr int SBO64 = 1024, SBO128 = 2048;   // 8-row-group stride of a K = 64 / K = 128 operand
 constexpr long long WAIT_LIMIT = 1ll << 22;  // mbarrier polls before a wait gives up
@@ -110,6 +111,29 @@ __device__ __forceinline__ void gemm(uint32_t d, const void* A, uint32_t a_sbo, 
                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),         \
                  "=r"(r[15])                                                                                     \
                : "r"(taddr))
+
+// 4 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ float4 tmem_ld4(uint32_t taddr) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  return make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+}
+
+// dst[0..64) += the 64 FP32 columns of this thread's TMEM lane at taddr, with
+// 16-byte atomics (dst 16-byte aligned).  The block starts at its own group of
+// four columns, so that blocks finishing together spread their atomics over 16
+// address groups instead of all adding into the same addresses at once.
+__device__ __forceinline__ void tmem_add_row64(uint32_t taddr, float* dst) {
+  const int rot = (int)(blockIdx.x & 15u);
+#pragma unroll 4
+  for (int k = 0; k < 16; ++k) {
+    const int c = ((k + rot) & 15) * 4;
+    atomicAdd(reinterpret_cast<float4*>(dst + c), tmem_ld4(taddr + (uint32_t)c));
+  }
+}
 
 // 64 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
@@ -500,18 +524,14 @@ __global__ void __launch_bounds__(MT, 1) k_mlp_grad(const float* __restrict__ P,
   }
   // ---- block results to global memory ----
   if (ok && any) {
-    // weight gradients: TMEM rows 0..63 (warps 0 and 1) hold dW[out][in]
+    // weight gradients: TMEM rows 0..63 (warps 0 and 1) hold dW[out][in]; every row
+    // offset below is a multiple of four floats (O_W1, O_W2, O_W3 and the row widths are)
     if (warp < 2) {
-      float w[64];
       const int o = t;
-      tmem_ld64(base + T_W1 + lanes, w);
-      for (int c = 0; c < WID; ++c) atomicAdd(grad + O_W1 + o * ENC + c, w[c]);
-      tmem_ld64(base + T_W1 + 64 + lanes, w);
-      for (int c = 0; c < WID; ++c) atomicAdd(grad + O_W1 + o * ENC + 64 + c, w[c]);
-      tmem_ld64(base + T_W2 + lanes, w);
-      for (int c = 0; c < WID; ++c) atomicAdd(grad + O_W2 + o * WID + c, w[c]);
-      tmem_ld64(base + T_W3 + lanes, w);
-      for (int c = 0; c < WID; ++c) atomicAdd(grad + O_W3 + o * WID + c, w[c]);
+      tmem_add_row64(base + T_W1 + lanes, grad + O_W1 + o * ENC);
+      tmem_add_row64(base + T_W1 + 64 + lanes, grad + O_W1 + o * ENC + 64);
+      tmem_add_row64(base + T_W2 + lanes, grad + O_W2 + o * WID);
+      tmem_add_row64(base + T_W3 + lanes, grad + O_W3 + o * WID);
     }
     for (int o = 16; o; o >>= 1) {
       my_loss += __shfl_xor_sync(~0u, my_loss, o);
@@ -712,6 +732,7 @@ int rc_mlp_infer(const float* params, const float* rec, int64_t n, float* y, voi
 
 int rc_mlp_grad(const float* params, const float* samples, int64_t n, float* grad, float* loss, void* cuda_stream) {
   if (!params || !grad || !loss || n < 0 || (n > 0 && !samples)) return TG_EINVAL;
+  if (reinterpret_cast<uintptr_t>(grad) & 15u) return TG_EINVAL;      // 16-byte atomics into grad
   if (n == 0) return TG_OK;
   try {
     const size_t shm = sizeof(rc::GradSmem);
