@@ -163,6 +163,14 @@ int tg_grid_import(const tg_volume_desc* vol, int32_t K, int64_t num_tets, const
  * grid must not be in use by work still queued on any stream. */
 void tg_grid_free(tg_grid* g);
 
+/* tg_release_build_memory - leb_build, leb_rebuild and tg_grid_channels take
+ * their buffers from a stream-ordered memory pool the library keeps per device,
+ * and freed buffers stay in it for the next build (a production-size build's
+ * temporaries are tens of GB; reusing them saves about 45 ms per build).  This
+ * call waits for the current device and returns the pool's unused memory to the
+ * driver.  The paper has no counterpart.  TG_ECUDA if CUDA fails. */
+int tg_release_build_memory(void);
+
 /*
  * tet_render - Sec. 3 (Algorithm 1) on the grid: W*H*spp paths, path (px, py, s)
  * for s in [sample_offset, sample_offset + spp), each a camera ray through the

@@ -6,12 +6,12 @@ this package builds it in-tree and binds it with ctypes.
 """
 from .api import (Batch, Grid, GridInfo, build_scene_grid, grid_import, grid_render, grid_trace_paths, leb_build, leb_rebuild,
                   rebuild_scene_grid,
-                  new_stats, stats_dict, tet_optical_depth, tet_render, tet_render_ext, tet_trace_ext_paths,
+                  new_stats, release_build_memory, stats_dict, tet_optical_depth, tet_render, tet_render_ext, tet_trace_ext_paths,
                   tet_trace_paths)
 from ._native import TetvolError
 from . import cache
 from .cache import RadianceCache
 
 __all__ = ["Batch", "Grid", "GridInfo", "TetvolError", "build_scene_grid", "grid_import", "grid_render", "grid_trace_paths",
-           "leb_build", "leb_rebuild", "rebuild_scene_grid", "new_stats", "stats_dict", "tet_optical_depth", "tet_render", "tet_trace_paths", "tet_render_ext", "tet_trace_ext_paths", "cache",
+           "leb_build", "leb_rebuild", "rebuild_scene_grid", "new_stats", "release_build_memory", "stats_dict", "tet_optical_depth", "tet_render", "tet_trace_paths", "tet_render_ext", "tet_trace_ext_paths", "cache",
            "RadianceCache"]

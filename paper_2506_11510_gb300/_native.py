@@ -63,6 +63,7 @@ SIGNATURES = {
     "grid_trace_paths": (C.c_int, [_VP, C.POINTER(TgVolumeDesc), C.POINTER(TgCamera), C.POINTER(TgMedium), _U64,
                                    _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "tet_optical_depth": (C.c_int, [_VP, _I64, _VP, _VP, _F, _VP, _VP, _VP, _I32, _VP, _VP]),
+    "tg_release_build_memory": (C.c_int, []),
     "tet_render_noalloc": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _I32, _U64, _I32, _VP, _VP,
                                      _VP]),
     "tg_grid_channels": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),

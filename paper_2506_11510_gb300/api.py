@@ -212,6 +212,11 @@ def grid_import(box_min, voxel_size, dims, K: int, codes, nbr, nid, plane, densi
     return Grid(h, desc, density_format)
 
 
+def release_build_memory():
+    """Return the device memory that builds keep for later builds (tg_release_build_memory)."""
+    N.check(N.lib().tg_release_build_memory(), "tg_release_build_memory")
+
+
 def new_stats(device=None) -> torch.Tensor:
     """Zeroed device tg_stats (8 x uint64 counters, as int64)."""
     return torch.zeros(len(N.STATS_FIELDS), dtype=torch.int64, device=device or "cuda")

@@ -1239,6 +1239,7 @@ extern "C" int tg_grid_channels(tg_grid* g, const float* density, const float* t
                                 const float* aniso, void* cuda_stream) {
   if (!g || !density) return TG_EINVAL;
   try {
+    tv::AllocScope scope((cudaStream_t)cuda_stream, tv::build_pool());
     return tv::grid_channels(g->impl, density, temperature, albedo, aniso, (cudaStream_t)cuda_stream);
   } catch (const tv::Error& e) {
     return e.code;
@@ -1287,6 +1288,7 @@ extern "C" int leb_build(const float* density, const tg_volume_desc* vol, const 
   if (!g) return TG_ENOMEM;
   int st;
   try {
+    tv::AllocScope scope((cudaStream_t)cuda_stream, tv::build_pool());
     st = tv::build_grid(density, vol, cam, target_footprint_px, variation_threshold, max_depth, density_format,
                         (cudaStream_t)cuda_stream, g->impl, nullptr);
   } catch (const tv::Error& e) {
@@ -1316,6 +1318,7 @@ extern "C" int leb_rebuild(const tg_grid* prev, const float* density, const tg_v
   if (!g) return TG_ENOMEM;
   int st;
   try {
+    tv::AllocScope scope((cudaStream_t)cuda_stream, tv::build_pool());
     st = tv::build_grid(density, vol, cam, target_footprint_px, variation_threshold, max_depth, density_format,
                         (cudaStream_t)cuda_stream, g->impl, &prev->impl);
   } catch (const tv::Error& e) {

@@ -2,9 +2,40 @@
 // info / export / import / free entry points.
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "walk_tet.cuh"
 
 namespace tv {
+
+thread_local cudaStream_t AllocScope::stream = nullptr;
+thread_local cudaMemPool_t AllocScope::pool = nullptr;
+thread_local bool AllocScope::active = false;
+
+static std::mutex pool_mu;
+static cudaMemPool_t build_pools[64] = {nullptr};
+
+cudaMemPool_t build_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(pool_mu);
+  if (!build_pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;                       // builds then allocate with cudaMalloc
+    }
+    unsigned long long keep = ~0ull;        // keep freed memory for the next build
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    build_pools[dev] = p;
+  }
+  return build_pools[dev];
+}
 
 GridImpl::~GridImpl() {
   int prev = -1;
@@ -214,6 +245,22 @@ int tg_grid_info(const tg_grid* g, int64_t* num_tets, int32_t* max_depth, int64_
 }
 
 void tg_grid_free(tg_grid* g) { delete g; }
+
+int tg_release_build_memory(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return TG_ECUDA;
+  }
+  cudaMemPool_t p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(pool_mu);
+    p = build_pools[dev];
+  }
+  if (!p) return TG_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(p, 0) != cudaSuccess) return TG_ECUDA;
+  return TG_OK;
+}
 
 int tet_render(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp, uint64_t seed,
                int32_t sample_offset, float* accum_sum, float* accum_sumsq, tg_stats* stats, void* cuda_stream) {

@@ -130,3 +130,26 @@ def test_build_refuses_pageable_host_memory():
     assert st == N.TG_EINVAL and not out.value
     with pytest.raises(TypeError):
         api.leb_build(torch.from_numpy(vol), s.box_min, s.voxel_size)
+
+
+def test_builds_reuse_their_memory_and_release_it():
+    """Builds take their buffers from the library's memory pool: a second build of
+    the same scene equals the first and takes (almost) no new device memory -- the
+    pool's memory is reused, not grown -- and tg_release_build_memory hands the
+    unused part back to the driver."""
+    import paper_2506_11510_gb300 as tv
+    s = W.scene("production_small")
+    vol = torch.from_numpy(scene_volume("production_small")).cuda()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    a = gpu_arrays(tv.build_scene_grid(s, vol))
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    b = gpu_arrays(tv.build_scene_grid(s, vol))
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    for k in FIELDS:
+        assert np.array_equal(a[k], b[k]), k
+    assert free1 - free2 <= 0.1 * max(free0 - free1, 0) + (8 << 20)
+    tv.release_build_memory()
+    assert torch.cuda.mem_get_info()[0] >= free2
