@@ -326,8 +326,12 @@ def run_ours(args):
     mean_launch_ms = sum(per_launch) / len(per_launch)
     achieved = steps_per_frame * BYTES_PER_STEP / (mean_launch_ms * 1e-3) / 1e9
     traffic = profiled_traffic(args.scene)
+    dram_frac = None if traffic is None else round(traffic / (mean_launch_ms * 1e-3) / 1e9 / peak, 4)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
+                "dram_frac": dram_frac,
+                "dram_frac_note": "measured DRAM bytes per launch (profiles/k_estimate_production_traffic.json) "
+                                  "over this run's mean launch time, against the same peak",
                 "kernel": "k_estimate<TetWalker> (persistent path tracer)",
                 "algorithmic_bytes": "32 B per tet step x %d steps per launch" % steps_per_frame,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
