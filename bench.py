@@ -747,12 +747,58 @@ def cache_leg(args, s, grid, dev, plain_ms):
     _, steps_ms = timed(steps)
     res["train_phases"] = {"trace_paths": n_tr, "trace_ms": round(trace_ms, 2), "steps": 128,
                            "samples_per_step": buf.shape[0] // 128, "steps_ms": round(steps_ms, 2)}
+    res["mlp_kernels"] = mlp_kernel_rates(dev)
     med = fixed["time_to_equal_rmse_ms_median"]
     res["time_to_equal_rmse_ms"] = med
     res["speedup_vs_plain"] = None if med is None else round(plain_ms / med, 3)
     res["headline"] = "fixed configuration (8 rounds, cache depth 1), median of 3 training seeds"
     res["timeouts"] = RC.timeouts()
     return res
+
+
+def mlp_kernel_rates(dev):
+    """The fused tensor-core MLP kernels alone (CUDA events, through the public API) at
+    the cache leg's sizes: one training step of 2^14 samples (and 2^18), and inference
+    over 2^20 records (one 1024^2 cached frame at 1 spp) and 2^22; FLOPs per record
+    2 (128*64 + 2*64*64) forward, three times that with the backward pass."""
+    import torch
+    from paper_2506_11510_gb300 import cache as RC, workloads as W
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak = float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        peak = 1900.0
+    st = torch.cuda.current_stream()
+    p = torch.from_numpy(W.mlp_init_params(1, b4=0.1)).to(dev)
+    fwd = 2 * (128 * 64 + 2 * 64 * 64)
+    out = {"bf16_peak_tflops": peak, "grad": [], "infer": []}
+
+    def timed(fn, reps):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e3 / reps
+
+    for n in (1 << 14, 1 << 18):
+        rec = torch.from_numpy(W.mlp_random_records(n, 3)).to(dev)
+        rec[:, 7] = 1.0
+        g = torch.zeros_like(p)
+        loss = torch.zeros(3, dtype=torch.float32, device=dev)
+        us = timed(lambda: RC.mlp_grad(p, rec, g, loss), 20)
+        tf = n * 3 * fwd / (us * 1e-6) / 1e12
+        out["grad"].append({"samples": n, "us": round(us, 1), "tflops": round(tf, 1), "frac": round(tf / peak, 4)})
+    for n in (1 << 20, 1 << 22):
+        rec = torch.from_numpy(W.mlp_random_records(n, 4)).to(dev)
+        y = torch.empty(n, dtype=torch.float32, device=dev)
+        us = timed(lambda: RC.mlp_infer(p, rec, y), 10)
+        tf = n * fwd / (us * 1e-6) / 1e12
+        out["infer"].append({"records": n, "us": round(us, 1), "tflops": round(tf, 1), "frac": round(tf / peak, 4)})
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -632,8 +632,25 @@ void launch_infer(const float* P, float* rec, long long n, float* y, cudaStream_
   const size_t shm = sizeof(InferSmem);
   // per device and cheap: set on every launch
   TV_CUDA(cudaFuncSetAttribute(k_mlp_infer<COMPOSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  TV_CUDA(cudaFuncSetAttribute(k_mlp_infer<COMPOSE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared));
   int per_sm = 0;
   TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_infer<COMPOSE>, MT, shm));
+  // The occupancy query answered one block per SM on GB300 although three fit (66.7 KB of
+  // shared memory and 106 registers per thread each); blocks that share an SM overlap one
+  // tile's epilogue with another's MMAs, so size the grid from the kernel's own footprint too.
+  {
+    int dev = 0, smem_sm = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    TV_CUDA(cudaGetDevice(&dev));
+    TV_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    TV_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    TV_CUDA(cudaFuncGetAttributes(&fa, k_mlp_infer<COMPOSE>));
+    const int by_smem = smem_sm / ((int)shm + (int)fa.sharedSizeBytes + reserved);
+    const int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * MT) : 1;
+    const int fit = by_smem < by_regs ? by_smem : by_regs;
+    if (fit > per_sm) per_sm = fit;
+  }
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;                   // 8 x 64 TMEM columns fill an SM's 512
   const long long ntiles = (n + MT - 1) / MT;
