@@ -188,7 +188,9 @@ int tg_release_build_memory(void);
  * tet_render_cached, tet_render_noalloc and batch entry points all refuse a range
  * that would wrap), TG_ECUDA.  A walk that exceeds its step
  * limit ends its path and is counted in stats->step_limit.
- * Calls that overlap on the same grid share its scratch counter: serialise them.
+ * Each call takes its own scratch (the path counter) from the library's
+ * stream-ordered pool on its stream, so calls on different streams may overlap,
+ * on the same grid or not.
  */
 int tet_render(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp, uint64_t seed,
                int32_t sample_offset, float* accum_sum, float* accum_sumsq, tg_stats* stats,
@@ -198,7 +200,7 @@ int tet_render(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int
  * grid_render - the regular-grid comparator (the "1024^3 regular grid" reference
  * of Sec. 4): the same estimator as tet_render, walking the voxels of the dense
  * volume with a 3D DDA instead of the tetrahedra.  Same arguments and semantics.
- * Uses a library-owned scratch counter per device: serialise overlapping calls.
+ * Like tet_render, each call takes its own scratch on its stream.
  */
 int grid_render(const float* density, const tg_volume_desc* vol, const tg_camera* cam, const tg_medium* med,
                 int32_t spp, uint64_t seed, int32_t sample_offset, float* accum_sum, float* accum_sumsq,
@@ -390,7 +392,7 @@ int tg_random_paths(uint64_t seed, int64_t n, int32_t width, int32_t height, int
  * survive (the draw after collision b is slot b of Philox stream 0x10000, counter
  * (sample, b / 4, 0x10000, 0)) and its throughput is divided by survive, so every
  * target keeps its expectation while the paths end sooner; 0 or 1: no roulette.
- * Asynchronous.  Shares the grid's scratch counter: serialise with other calls.
+ * Asynchronous; each call takes its own scratch on its stream.
  * TG_EINVAL for survive outside [0, 1].
  */
 int tet_cache_samples(const tg_grid* g, const tg_camera* cam, const tg_medium* med, uint64_t seed, int64_t n,
@@ -444,10 +446,10 @@ int rc_adam(float* params, float* m, float* v, float* grad, float* loss, int32_t
  * pixels, samples, random numbers and accumulation), but every path that
  * reaches its cache_depth-th collision ends there into the cache:
  * L + beta * max(R(x, d), 0) per path.  Three launches: the tracer writing one
- * record per path into the grid's scratch pool (32 bytes x W x H x spp, grown
- * on first use and kept with the grid), the fused MLP completing the records,
- * and a per-pixel sum in sample order.  Asynchronous; serialise calls on the
- * same grid.
+ * record per path (32 bytes x W x H x spp, this call's own scratch from the
+ * library's stream-ordered pool, given back on the stream after the last
+ * launch), the fused MLP completing the records, and a per-pixel sum in sample
+ * order.  Asynchronous; calls on different streams may overlap.
  */
 int tet_render_cached(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int32_t spp, uint64_t seed,
                       int32_t sample_offset, int32_t cache_depth, const float* params, float* accum_sum,

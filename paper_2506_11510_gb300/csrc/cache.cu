@@ -697,13 +697,13 @@ int tet_cache_samples(const tg_grid* g, const tg_camera* cam, const tg_medium* m
     EstParams ep = est_params(G, *cam, *med, seed);
     ep.spp = 1;
     ep.total = n;
-    ep.counter = G.scratch;
+    CallCounter counter(st);
+    ep.counter = counter.p;
     ep.px = px; ep.py = py; ep.ps = sample;
     ep.outL = L;
     ep.vtx_cap = max_vertices;
     ep.vtx = samples;
     ep.survive = survive;
-    TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
     run_tet<MODE_TRACE>(G, ep, st);
   } catch (const Error& e) {
     return e.code;
@@ -725,11 +725,11 @@ int tet_cache_queries(const tg_grid* g, const tg_camera* cam, const tg_medium* m
     EstParams ep = est_params(G, *cam, *med, seed);
     ep.spp = 1;
     ep.total = n;
-    ep.counter = G.scratch;
+    CallCounter counter(st);
+    ep.counter = counter.p;
     ep.px = px; ep.py = py; ep.ps = sample;
     ep.cache_depth = cache_depth;
     ep.cache_rec = rec;
-    TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
     run_tet<MODE_TRACE>(G, ep, st);
   } catch (const Error& e) {
     return e.code;
@@ -791,29 +791,25 @@ int tet_render_cached(const tg_grid* g, const tg_camera* cam, const tg_medium* m
       !accum_sum)
     return TG_EINVAL;
   try {
-    GridImpl& G = const_cast<GridImpl&>(g->impl);
+    const GridImpl& G = g->impl;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (spp == 0 || G.n == 0) return TG_OK;
     const long long npix = (long long)cam->width * cam->height;
     const long long total = npix * spp;
-    const size_t need = (size_t)total * 8;
-    if (G.pool_floats < need) {
-      if (G.pool) { TV_CUDA(cudaFree(G.pool)); G.pool = nullptr; G.pool_floats = 0; }
-      TV_CUDA(cudaMalloc(&G.pool, need * sizeof(float)));
-      G.pool_floats = need;
-    }
+    // the frame's path records (32 B each), this call's own
+    CallScratch<float> recs((size_t)total * 8, st);
     EstParams ep = est_params(G, *cam, *med, seed);
     ep.spp = spp;
     ep.sample_offset = sample_offset;
     ep.total = total;
-    ep.counter = G.scratch;
+    CallCounter counter(st);
+    ep.counter = counter.p;
     ep.stats = stats;
     ep.cache_depth = cache_depth;
-    ep.cache_rec = G.pool;
-    TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
+    ep.cache_rec = recs.p;
     run_tet<MODE_CACHED>(G, ep, st);
-    rc::launch_infer<true>(params, G.pool, total, nullptr, st);
-    rc::k_cache_accum<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(G.pool, npix, spp, cam->width, cam->height,
+    rc::launch_infer<true>(params, recs.p, total, nullptr, st);
+    rc::k_cache_accum<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(recs.p, npix, spp, cam->width, cam->height,
                                                                        accum_sum, accum_sumsq);
     TV_LAUNCH();
   } catch (const Error& e) {

@@ -59,6 +59,33 @@ inline void dev_free(void* p) {
   else cudaFree(p);
 }
 
+// Scratch of one call (a renderer's path counter, a cached frame's path
+// records): taken from the library's stream-ordered pool on the call's stream
+// and given back on that stream after the call's last kernel, so calls on
+// other streams -- on the same grid or not -- never share it.
+template <class T>
+struct CallScratch {
+  T* p = nullptr;
+  cudaStream_t st;
+  CallScratch(size_t count, cudaStream_t s) : st(s) {
+    cudaMemPool_t pool = build_pool();
+    void* q = nullptr;
+    if (pool) check(cudaMallocFromPoolAsync(&q, count * sizeof(T), pool, s));
+    else check(cudaMallocAsync(&q, count * sizeof(T), s));
+    p = static_cast<T*>(q);
+  }
+  CallScratch(const CallScratch&) = delete;
+  CallScratch& operator=(const CallScratch&) = delete;
+  ~CallScratch() { if (p) cudaFreeAsync(p, st); }
+};
+
+// A zeroed path-id counter for one persistent-estimator launch on stream s.
+struct CallCounter : CallScratch<unsigned long long> {
+  explicit CallCounter(cudaStream_t s) : CallScratch<unsigned long long>(1, s) {
+    check(cudaMemsetAsync(p, 0, sizeof(unsigned long long), s));
+  }
+};
+
 // Device allocation owned by the library (RAII).
 template <class T>
 struct DevBuf {
@@ -115,8 +142,6 @@ struct GridImpl {
   unsigned long long* scratch = nullptr; // work counter of the persistent renderer
   int32_t* locator = nullptr;            // cell of each locator-grid cell centre (loc_R per cube edge)
   int loc_R = 0;
-  float* pool = nullptr;                 // scratch pool of the cached renderer (grown on demand)
-  size_t pool_floats = 0;
   float4* chan = nullptr;                // extra channels per cell: temperature, albedo, g, 0
   float* vmaj = nullptr;                 // voxel majorant per cell
   int chan_mask = 0;                     // 1 temperature, 2 albedo, 4 g, 8 majorants present

@@ -7,19 +7,6 @@
 
 namespace tv {
 
-// One work counter per device for the comparator, allocated on first use and
-// kept until the process exits.
-static unsigned long long* dda_counter() {
-  static std::mutex mu;
-  static std::vector<unsigned long long*> per_dev;
-  int dev = 0;
-  TV_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(mu);
-  if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1, nullptr);
-  if (!per_dev[dev]) TV_CUDA(cudaMalloc(&per_dev[dev], 4 * sizeof(unsigned long long)));
-  return per_dev[dev];
-}
-
 static bool vol_setup(const tg_volume_desc* v, VoxParams* p, double* cube, float box_min[3]) {
   if (!v || v->nx <= 0 || v->ny <= 0 || v->nz <= 0 || !(v->voxel_size > 0)) return false;
   if ((long long)v->nx * v->ny * v->nz >= (1ll << 31)) return false;
@@ -70,11 +57,11 @@ int grid_render(const float* density, const tg_volume_desc* vol, const tg_camera
     ep.spp = spp;
     ep.sample_offset = sample_offset;
     ep.total = (long long)cam->width * cam->height * spp;
-    ep.counter = dda_counter();
+    CallCounter counter(st);
+    ep.counter = counter.p;
     ep.sum = accum_sum;
     ep.sumsq = accum_sumsq;
     ep.stats = stats;
-    TV_CUDA(cudaMemsetAsync(ep.counter, 0, sizeof(unsigned long long), st));
     launch_estimate<VoxelWalker, MODE_RENDER>(p, ep, st);
   } catch (const Error& e) {
     return e.code;
@@ -98,10 +85,10 @@ int grid_trace_paths(const float* density, const tg_volume_desc* vol, const tg_c
     EstParams ep = dda_est(*cam, *med, seed, cube, bmin);
     ep.spp = 1;
     ep.total = n;
-    ep.counter = dda_counter();
+    CallCounter counter(st);
+    ep.counter = counter.p;
     ep.px = px; ep.py = py; ep.ps = sample;
     ep.outL = L; ep.outFlags = flags; ep.outColl = collisions; ep.outSteps = steps;
-    TV_CUDA(cudaMemsetAsync(ep.counter, 0, sizeof(unsigned long long), st));
     launch_estimate<VoxelWalker, MODE_TRACE>(p, ep, st);
   } catch (const Error& e) {
     return e.code;

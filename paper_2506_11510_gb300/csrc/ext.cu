@@ -41,11 +41,11 @@ int tet_render_ext(const tg_grid* g, const tg_camera* cam, const tg_medium* med,
     ep.spp = spp;
     ep.sample_offset = sample_offset;
     ep.total = (long long)cam->width * cam->height * spp;
-    ep.counter = G.scratch;
+    CallCounter counter(st);
+    ep.counter = counter.p;
     ep.sum = accum_sum;
     ep.sumsq = accum_sumsq;
     ep.stats = stats;
-    TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
     run_tet<MODE_RENDER, true>(G, ep, st);
   } catch (const Error& e) {
     return e.code;
@@ -66,10 +66,10 @@ int tet_trace_ext_paths(const tg_grid* g, const tg_camera* cam, const tg_medium*
     if (n == 0) return TG_OK;
     ep.spp = 1;
     ep.total = n;
-    ep.counter = G.scratch;
+    CallCounter counter(st);
+    ep.counter = counter.p;
     ep.px = px; ep.py = py; ep.ps = sample;
     ep.outL = L; ep.outFlags = flags; ep.outColl = collisions; ep.outSteps = steps;
-    TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
     run_tet<MODE_TRACE, true>(G, ep, st);
   } catch (const Error& e) {
     return e.code;

@@ -41,7 +41,7 @@ GridImpl::~GridImpl() {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator, pool, chan, vmaj,
+  void* ptrs[] = {rec, codes, verts, tag, count, qmin, qmax, sum, majorant, scratch, locator, chan, vmaj,
                   node_code, node_sum, node_cnt, node_mn, node_mx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -273,11 +273,11 @@ int tet_render(const tg_grid* g, const tg_camera* cam, const tg_medium* med, int
   ep.spp = spp;
   ep.sample_offset = sample_offset;
   ep.total = (long long)cam->width * cam->height * spp;
-  ep.counter = G.scratch;
+  CallCounter counter(st);
+  ep.counter = counter.p;
   ep.sum = accum_sum;
   ep.sumsq = accum_sumsq;
   ep.stats = stats;
-  TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
   run_tet<MODE_RENDER>(G, ep, st);
   return TG_OK;
   TV_API_END
@@ -297,11 +297,11 @@ int tet_trace_paths(const tg_grid* g, const tg_camera* cam, const tg_medium* med
   EstParams ep = est_params(G, *cam, *med, seed);
   ep.spp = 1;
   ep.total = n;
-  ep.counter = G.scratch;
+  CallCounter counter(st);
+  ep.counter = counter.p;
   ep.px = px; ep.py = py; ep.ps = sample;
   ep.outL = L; ep.outFlags = flags; ep.outColl = collisions; ep.outSteps = steps;
   ep.seq = seq; ep.seq_cap = seq ? seq_cap : 0; ep.seq_len = seq_len;
-  TV_CUDA(cudaMemsetAsync(G.scratch, 0, sizeof(unsigned long long), st));
   run_tet<MODE_TRACE>(G, ep, st);
   return TG_OK;
   TV_API_END

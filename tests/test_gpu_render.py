@@ -127,3 +127,26 @@ def test_zero_work_calls_are_noops(tiny):
     assert float(img.abs().sum()) == 0.0
     out = tv.tet_trace_paths(grid, s.camera, s.medium, 1, [], [], [])
     assert out["L"].numel() == 0
+
+
+def test_concurrent_renders_of_one_grid_on_two_streams(tiny):
+    """Each render call takes its own path counter on its own stream, so two
+    frames of the same grid rendered concurrently on two streams are each the
+    frame a lone call renders (only the order of the float atomics differs)."""
+    import paper_2506_11510_gb300 as tv
+    s, grid, _ = tiny
+    ref, ref2 = tv.tet_render(grid, s.camera, s.medium, s.spp, s.render_seed)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for k, st in enumerate(streams):
+        with torch.cuda.stream(st):
+            a = torch.zeros_like(ref)
+            a2 = torch.zeros_like(ref)
+            for _ in range(4):
+                tv.tet_render(grid, s.camera, s.medium, s.spp, s.render_seed, 0, a, a2)
+            outs.append((a, a2))
+    torch.cuda.synchronize()
+    for a, a2 in outs:
+        assert torch.allclose(a, 4 * ref, rtol=1e-5, atol=1e-6)
+        assert torch.allclose(a2, 4 * ref2, rtol=1e-5, atol=1e-6)
