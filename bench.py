@@ -55,6 +55,8 @@ def parse():
                    help="collision limits of training paths tried besides the medium's (empty: none)")
     p.add_argument("--cache-ref-pixels", type=int, default=4096)
     p.add_argument("--cache-ref-spp", type=int, default=4096)
+    p.add_argument("--mlp-kernels-only", action="store_true",
+                   help="only time the radiance cache's MLP kernels (no grid, no frame) and print their rates")
     return p.parse_args()
 
 
@@ -999,6 +1001,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mlp_kernels_only:
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_device(dev)
+        print(json.dumps({"mlp_kernels": mlp_kernel_rates(dev)}))
     else:
         run_ours(args)
 

@@ -322,10 +322,21 @@ __device__ __forceinline__ void row_interval(const int nrm[4][3], const long lon
   *xb = (int)max(b, a - 1);
 }
 
+// What the work items of one leaf share (written once per leaf by pass 1, read
+// by every work item of pass 2): its voxel box, its four face planes n . p <= rhs
+// (n in {0, +-1}^3, two bits per component holding n + 1) and its index.
+struct __align__(16) ScanDesc {
+  int lo[3], hi[3];
+  uint32_t nrm;
+  int leaf;
+  long long rhs[4];
+};
+
 // A3 statistics, pass 1: work items of the new leaves (ROWS rows of the leaf's
-// voxel box each); reset their statistics
+// voxel box each) and what they share; reset their statistics
 template <bool BOX>
-__global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo g, unsigned long long* chunks) {
+__global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo g, unsigned long long* chunks,
+                             ScanDesc* desc) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   const long long i = list ? list[j] : j;
@@ -336,8 +347,24 @@ __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo
   if (hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2])
     rows = (long long)(hi[1] - lo[1] + 1) * (long long)(hi[2] - lo[2] + 1);
   // small boxes are scanned by one thread in k_stats_finish
-  chunks[j] = small_box(lo, hi) ? 0ull : (unsigned long long)((rows + ROWS - 1) / ROWS);
+  const bool small = small_box(lo, hi);
+  chunks[j] = small ? 0ull : (unsigned long long)((rows + ROWS - 1) / ROWS);
   L.cnt[i] = 0; L.sum[i] = 0; L.mn[i] = 0xFFFFFFFFu; L.mx[i] = 0;
+  if (small) return;
+  ScanDesc d;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) { d.lo[a] = lo[a]; d.hi[a] = hi[a]; }
+  d.nrm = 0;
+  d.leaf = (int)i;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    int n[3] = {0, 0, 0};
+    d.rhs[f] = 0;
+    if (!BOX) face_plane(x, f, n, &d.rhs[f]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d.nrm |= (uint32_t)(n[a] + 1) << (2 * (3 * f + a));
+  }
+  desc[j] = d;
 }
 
 // A3 statistics, between the passes: the leaf (position in the scan list) that
@@ -364,7 +391,7 @@ __device__ __forceinline__ void row_tail(const uint32_t* __restrict__ row, int a
 // is at least 32 voxels wide (coalesced; the first 32 voxels of four rows are
 // loaded together), else by each lane along its row.
 template <bool BOX>
-__global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long* list, long long m,
+__global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const ScanDesc* __restrict__ desc,
                                                     const unsigned long long* chunk_off, const int* __restrict__ owner,
                                                     unsigned long long total, const uint32_t* __restrict__ q, Geo g) {
   const unsigned lane = threadIdx.x & 31u;
@@ -372,15 +399,19 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const long long*
   const int hs = g.K - g.m - 1;                     // h = 2^hs
   for (long long c = (long long)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5); c < (long long)total; c += warps) {
     const long long j = owner[c];                   // chunk_off[j] <= c < chunk_off[j + 1]
-    const long long i = list ? list[j] : j;
-    int x[4][3], lo[3], hi[3];
-    load_tet(L.v, i, x);
-    leaf_box<BOX>(x, g, lo, hi);
+    const ScanDesc& D = desc[j];
+    const long long i = D.leaf;
+    const int lo[3] = {D.lo[0], D.lo[1], D.lo[2]}, hi[3] = {D.hi[0], D.hi[1], D.hi[2]};
     int nrm[4][3];
     long long rhs[4];
     if (!BOX) {
+      const uint32_t nb = D.nrm;
 #pragma unroll
-      for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
+      for (int f = 0; f < 4; ++f) {
+        rhs[f] = D.rhs[f];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nrm[f][a] = (int)((nb >> (2 * (3 * f + a))) & 3u) - 1;
+      }
     }
     const long long wy = hi[1] - lo[1] + 1;
     const long long rows = wy * (hi[2] - lo[2] + 1);
@@ -843,14 +874,14 @@ struct Scanner {
 // Pass 2 of the statistics over `total` work items (offsets off[0..m]): the
 // owner of every work item, then the scan.
 template <bool BOX>
-void stats_scan(LeafPtrs L, const long long* list, long long m, const unsigned long long* off,
+void stats_scan(LeafPtrs L, const ScanDesc* desc, long long m, const unsigned long long* off,
                 unsigned long long total, DevBuf<int>& owner, const uint32_t* q, const Geo& g, int sms,
                 cudaStream_t st) {
   owner.ensure(total);
   k_chunk_owner<<<blocks_for(m), TPB, 0, st>>>(off, m, owner.p);
   TV_LAUNCH();
   const long long wblocks = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
-  k_stats_scan<BOX><<<(unsigned)wblocks, TPB, 0, st>>>(L, list, m, off, owner.p, total, q, g);
+  k_stats_scan<BOX><<<(unsigned)wblocks, TPB, 0, st>>>(L, desc, off, owner.p, total, q, g);
   TV_LAUNCH();
 }
 
@@ -866,7 +897,8 @@ struct LookupBufs {
 // only the others are scanned.
 void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const uint32_t* q, const Crit& C,
                          Scanner& scan, DevBuf<unsigned long long>& chunks, DevBuf<unsigned long long>& off,
-                         DevBuf<int>& owner, cudaStream_t st, int sms, const PrevNodes* prev, LookupBufs& lk) {
+                         DevBuf<int>& owner, DevBuf<ScanDesc>& desc, cudaStream_t st, int sms,
+                         const PrevNodes* prev, LookupBufs& lk) {
   if (m == 0) return;
   LeafPtrs L = Lv.ptrs();
   const long long* slist = list;              // leaves to scan
@@ -893,14 +925,15 @@ void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const u
   if (sm > 0) {
     chunks.ensure(sm + 1);
     off.ensure(sm + 1);
-    k_stats_prep<false><<<blocks_for(sm), TPB, 0, st>>>(L, slist, sm, C.g, chunks.p);
+    desc.ensure(sm);
+    k_stats_prep<false><<<blocks_for(sm), TPB, 0, st>>>(L, slist, sm, C.g, chunks.p, desc.p);
     TV_LAUNCH();
     TV_CUDA(cudaMemsetAsync(chunks.p + sm, 0, sizeof(unsigned long long), st));
     scan.exclusive(chunks.p, off.p, sm + 1, st);
     unsigned long long total = 0;
     TV_CUDA(cudaMemcpyAsync(&total, off.p + sm, sizeof total, cudaMemcpyDeviceToHost, st));
     TV_CUDA(cudaStreamSynchronize(st));
-    if (total) stats_scan<false>(L, slist, sm, off.p, total, owner, q, C.g, sms, st);
+    if (total) stats_scan<false>(L, desc.p, sm, off.p, total, owner, q, C.g, sms, st);
   }
   k_stats_finish<<<blocks_for(m), TPB, 0, st>>>(L, list, m, q, C, known);
   TV_LAUNCH();
@@ -1005,12 +1038,13 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   Scanner scan;
   DevBuf<unsigned long long> chunks, off, marks, pos;
   DevBuf<int> owner;
+  DevBuf<ScanDesc> desc;
   DevBuf<long long> newlist;
   // interior nodes, appended as leaves are split
   DevBuf<unsigned long long> acode, asum;
   DevBuf<uint32_t> acnt, amn, amx;
   long long nint = 0;
-  stats_and_criterion(A, nullptr, nroots, q.p, C, scan, chunks, off, owner, st, sms, pp, lk);
+  stats_and_criterion(A, nullptr, nroots, q.p, C, scan, chunks, off, owner, desc, st, sms, pp, lk);
 
   long long N = nroots;
   const int max_rounds = 4 * max_depth + 16;
@@ -1067,7 +1101,7 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     std::swap(A, B);
     N += M;
     nint += M;
-    stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, owner, st, sms, pp, lk);
+    stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, owner, desc, st, sms, pp, lk);
   }
 
   // ---- interior-node statistics sorted by code (for rebuilds) ----
@@ -1184,6 +1218,7 @@ int grid_channels(GridImpl& G, const float* density, const float* temperature, c
   DevBuf<uint32_t> q(nvox), cnt(N), mn(N), mx(N);
   DevBuf<unsigned long long> sum(N), chunks, off;
   DevBuf<int> owner;
+  DevBuf<ScanDesc> desc;
   DevBuf<float> chan((size_t)N * 4), vmaj(N);
   TV_CUDA(cudaMemsetAsync(chan.p, 0, (size_t)N * 16, st));
   LeafPtrs L{reinterpret_cast<int4*>(G.verts), G.codes, nullptr, cnt.p, mn.p, mx.p, sum.p, nullptr};
@@ -1192,8 +1227,9 @@ int grid_channels(GridImpl& G, const float* density, const float* temperature, c
   auto leaf_stats = [&](bool box) {
     chunks.ensure(N + 1);
     off.ensure(N + 1);
-    if (box) k_stats_prep<true><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p);
-    else k_stats_prep<false><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p);
+    desc.ensure(N);
+    if (box) k_stats_prep<true><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p);
+    else k_stats_prep<false><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p);
     TV_LAUNCH();
     TV_CUDA(cudaMemsetAsync(chunks.p + N, 0, sizeof(unsigned long long), st));
     scan.exclusive(chunks.p, off.p, N + 1, st);
@@ -1201,8 +1237,8 @@ int grid_channels(GridImpl& G, const float* density, const float* temperature, c
     TV_CUDA(cudaMemcpyAsync(&total, off.p + N, sizeof total, cudaMemcpyDeviceToHost, st));
     TV_CUDA(cudaStreamSynchronize(st));
     if (total) {
-      if (box) stats_scan<true>(L, nullptr, N, off.p, total, owner, q.p, g, sms, st);
-      else stats_scan<false>(L, nullptr, N, off.p, total, owner, q.p, g, sms, st);
+      if (box) stats_scan<true>(L, desc.p, N, off.p, total, owner, q.p, g, sms, st);
+      else stats_scan<false>(L, desc.p, N, off.p, total, owner, q.p, g, sms, st);
     }
     if (box) k_leaf_small<true><<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g);
     else k_leaf_small<false><<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g);
