@@ -256,15 +256,16 @@ __global__ void k_rehash(const unsigned long long* old, long long oldcap, unsign
 }
 
 // voxel index range of the centres inside [lo, hi] (units of 2^-K) along one axis
-__device__ __forceinline__ void voxel_range(long long lo, long long hi, int h, int dim, int* a, int* b) {
-  // centre (2i + 1) h in [lo, hi]  <=>  (lo - h) / 2h <= i <= (hi - h) / 2h
-  const long long two_h = 2ll * h;
-  long long ilo = lo - h >= 0 ? (lo - h + two_h - 1) / two_h : -((h - lo) / two_h);
-  long long ihi = hi - h >= 0 ? (hi - h) / two_h : -((h - hi + two_h - 1) / two_h);
+__device__ __forceinline__ void voxel_range(int lo, int hi, int h, int dim, int* a, int* b) {
+  // centre (2i + 1) h in [lo, hi]  <=>  ceil((lo - h) / 2h) <= i <= floor((hi - h) / 2h); 2h = 2^s, and
+  // coordinates are below 2^20, so both are exact shifts of 32-bit values
+  const int s = __ffs(h);                           // log2(2h)
+  int ilo = -((h - lo) >> s);
+  int ihi = (hi - h) >> s;
   if (ilo < 0) ilo = 0;
   if (ihi > dim - 1) ihi = dim - 1;
-  *a = (int)ilo;
-  *b = (int)ihi;
+  *a = ilo;
+  *b = ihi;
 }
 
 __device__ __forceinline__ void tet_box(const int x[4][3], const Geo& g, int lo[3], int hi[3]) {
@@ -306,20 +307,51 @@ __device__ __forceinline__ bool small_box(const int lo[3], const int hi[3]) {
 // B = rhs - n_y (2j+1) h - n_z (2k+1) h, a face with n_x = 1 gives
 // i <= floor((F - 1) / 2), n_x = -1 gives i >= ceil((-F - 1) / 2), and n_x = 0
 // keeps the row iff B >= 0.
-__device__ __forceinline__ void row_interval(const int nrm[4][3], const long long rhs[4], int hs, int jj, int kk,
+// (Coordinates are at most 2^19 (the build refuses larger grids), so |rhs| < 2^21 and
+// every term fits a 32-bit integer.)
+__device__ __forceinline__ void row_interval(const int nrm[4][3], const int rhs[4], int hs, int jj, int kk,
                                              int x0, int x1, int* xa, int* xb) {
-  const long long Py = (2ll * jj + 1) << hs, Pz = (2ll * kk + 1) << hs;
-  long long a = x0, b = x1;
+  const int Py = (2 * jj + 1) << hs, Pz = (2 * kk + 1) << hs;
+  int a = x0, b = x1;
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    const long long B = rhs[f] - nrm[f][1] * Py - nrm[f][2] * Pz;
-    const long long F = B >> hs;                 // floor(B / h)
+    const int B = rhs[f] - nrm[f][1] * Py - nrm[f][2] * Pz;
+    const int F = B >> hs;                       // floor(B / h)
     if (nrm[f][0] > 0) b = min(b, (F - 1) >> 1);
     else if (nrm[f][0] < 0) a = max(a, -((F + 1) >> 1));
     else if (B < 0) b = a - 1;
   }
-  *xa = (int)a;
-  *xb = (int)max(b, a - 1);
+  *xa = a;
+  *xb = max(b, a - 1);
+}
+
+// The four outward face planes of a tet as n . p <= rhs (32-bit rhs, see above).
+__device__ __forceinline__ void face_planes32(const int x[4][3], int nrm[4][3], int rhs[4]) {
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    long long r = 0;
+    face_plane(x, f, nrm[f], &r);
+    rhs[f] = (int)r;
+  }
+}
+
+// Statistics of a leaf whose box is small (small_box), by one thread.
+template <bool BOX>
+__device__ __forceinline__ void small_box_stats(const int lo[3], const int hi[3], const int nrm[4][3],
+                                                const int rhs[4], const uint32_t* __restrict__ q, const Geo& g,
+                                                uint32_t& cnt, unsigned long long& sum, uint32_t& mn, uint32_t& mx) {
+  const int hs = g.K - g.m - 1;
+  cnt = 0; sum = 0; mn = 0xFFFFFFFFu; mx = 0;
+  for (int kk = lo[2]; kk <= hi[2]; ++kk)
+    for (int jj = lo[1]; jj <= hi[1]; ++jj) {
+      int xa = lo[0], xb = hi[0];
+      if (!BOX) row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
+      const uint32_t* row = q + ((size_t)kk * g.ny + jj) * g.nx;
+      for (int ii = xa; ii <= xb; ++ii) {
+        const uint32_t v = __ldg(row + ii);
+        ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+      }
+    }
 }
 
 // What the work items of one leaf share (written once per leaf by pass 1, read
@@ -329,28 +361,36 @@ struct __align__(16) ScanDesc {
   int lo[3], hi[3];
   uint32_t nrm;
   int leaf;
-  long long rhs[4];
+  int rhs[4];
 };
 
-// A3 statistics, pass 1: work items of the new leaves (ROWS rows of the leaf's
-// voxel box each) and what they share; reset their statistics
+// A3 statistics, pass 1: the statistics of a new leaf with a small voxel box
+// (by this thread), or the work items of a larger one (ROWS rows of its box
+// each) and what they share, its statistics reset for pass 2
 template <bool BOX>
 __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo g, unsigned long long* chunks,
-                             ScanDesc* desc) {
+                             ScanDesc* desc, const uint32_t* __restrict__ q) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   const long long i = list ? list[j] : j;
   int x[4][3], lo[3], hi[3];
   load_tet(L.v, i, x);
   leaf_box<BOX>(x, g, lo, hi);
-  long long rows = 0;
-  if (hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2])
-    rows = (long long)(hi[1] - lo[1] + 1) * (long long)(hi[2] - lo[2] + 1);
-  // small boxes are scanned by one thread in k_stats_finish
-  const bool small = small_box(lo, hi);
-  chunks[j] = small ? 0ull : (unsigned long long)((rows + ROWS - 1) / ROWS);
+  const bool empty = !(hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2]);
+  const bool small = !empty && small_box(lo, hi);
+  int nrm[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, rhs[4] = {0, 0, 0, 0};
+  if (!BOX && !empty) face_planes32(x, nrm, rhs);
+  if (empty || small) {
+    chunks[j] = 0;
+    uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
+    unsigned long long sum = 0;
+    if (small) small_box_stats<BOX>(lo, hi, nrm, rhs, q, g, cnt, sum, mn, mx);
+    L.cnt[i] = cnt; L.sum[i] = sum; L.mn[i] = mn; L.mx[i] = mx;
+    return;
+  }
+  const long long rows = (long long)(hi[1] - lo[1] + 1) * (long long)(hi[2] - lo[2] + 1);
+  chunks[j] = (unsigned long long)((rows + ROWS - 1) / ROWS);
   L.cnt[i] = 0; L.sum[i] = 0; L.mn[i] = 0xFFFFFFFFu; L.mx[i] = 0;
-  if (small) return;
   ScanDesc d;
 #pragma unroll
   for (int a = 0; a < 3; ++a) { d.lo[a] = lo[a]; d.hi[a] = hi[a]; }
@@ -358,11 +398,9 @@ __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo
   d.leaf = (int)i;
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    int n[3] = {0, 0, 0};
-    d.rhs[f] = 0;
-    if (!BOX) face_plane(x, f, n, &d.rhs[f]);
+    d.rhs[f] = rhs[f];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d.nrm |= (uint32_t)(n[a] + 1) << (2 * (3 * f + a));
+    for (int a = 0; a < 3; ++a) d.nrm |= (uint32_t)(nrm[f][a] + 1) << (2 * (3 * f + a));
   }
   desc[j] = d;
 }
@@ -403,7 +441,7 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const ScanDesc* 
     const long long i = D.leaf;
     const int lo[3] = {D.lo[0], D.lo[1], D.lo[2]}, hi[3] = {D.hi[0], D.hi[1], D.hi[2]};
     int nrm[4][3];
-    long long rhs[4];
+    int rhs[4];
     if (!BOX) {
       const uint32_t nb = D.nrm;
 #pragma unroll
@@ -470,48 +508,6 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const ScanDesc* 
   }
 }
 
-// Statistics of a leaf whose box is small (small_box), by one thread; other
-// leaves are left to k_stats_scan.
-template <bool BOX>
-__device__ __forceinline__ void small_leaf_stats(LeafPtrs L, long long i, const int x[4][3],
-                                                 const uint32_t* __restrict__ q, const Geo& g) {
-  int lo[3], hi[3];
-  leaf_box<BOX>(x, g, lo, hi);
-  if (!(hi[0] >= lo[0] && hi[1] >= lo[1] && hi[2] >= lo[2] && small_box(lo, hi))) return;
-  int nrm[4][3];
-  long long rhs[4];
-  if (!BOX) {
-#pragma unroll
-    for (int f = 0; f < 4; ++f) face_plane(x, f, nrm[f], &rhs[f]);
-  }
-  const int hs = g.K - g.m - 1;
-  uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
-  unsigned long long sum = 0;
-  for (int kk = lo[2]; kk <= hi[2]; ++kk)
-    for (int jj = lo[1]; jj <= hi[1]; ++jj) {
-      int xa = lo[0], xb = hi[0];
-      if (!BOX) row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
-      const uint32_t* row = q + ((size_t)kk * g.ny + jj) * g.nx;
-      for (int ii = xa; ii <= xb; ++ii) {
-        const uint32_t v = __ldg(row + ii);
-        ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
-      }
-    }
-  L.cnt[i] = cnt; L.sum[i] = sum; L.mn[i] = mn; L.mx[i] = mx;
-}
-
-template <bool BOX>
-__global__ void k_leaf_small(LeafPtrs L, long long m, const uint32_t* __restrict__ q, Geo g) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  int x[4][3];
-  load_tet(L.v, i, x);
-  small_leaf_stats<BOX>(L, i, x, q, g);
-}
-
-// Per-tet channel c of the final grid: the mean of the quantised channel over D
-// (the voxel of the centroid if D is empty), as the density; g = 2a - 1 in
-// [-0.99, 0.99] for the anisotropy channel.
 __global__ void k_channel_store(LeafPtrs L, long long m, const uint32_t* __restrict__ q, Geo g, int c,
                                 float* __restrict__ chan) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -650,7 +646,6 @@ __global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, c
   int x[4][3];
   load_tet(L.v, i, x);
   const Geo& g = C.g;
-  if (!known || !known[j]) small_leaf_stats<false>(L, i, x, q, g);
   if (L.cnt[i] == 0) {
     const int dims[3] = {g.nx, g.ny, g.nz};
     int idx[3];
@@ -926,7 +921,7 @@ void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const u
     chunks.ensure(sm + 1);
     off.ensure(sm + 1);
     desc.ensure(sm);
-    k_stats_prep<false><<<blocks_for(sm), TPB, 0, st>>>(L, slist, sm, C.g, chunks.p, desc.p);
+    k_stats_prep<false><<<blocks_for(sm), TPB, 0, st>>>(L, slist, sm, C.g, chunks.p, desc.p, q);
     TV_LAUNCH();
     TV_CUDA(cudaMemsetAsync(chunks.p + sm, 0, sizeof(unsigned long long), st));
     scan.exclusive(chunks.p, off.p, sm + 1, st);
@@ -1228,8 +1223,8 @@ int grid_channels(GridImpl& G, const float* density, const float* temperature, c
     chunks.ensure(N + 1);
     off.ensure(N + 1);
     desc.ensure(N);
-    if (box) k_stats_prep<true><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p);
-    else k_stats_prep<false><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p);
+    if (box) k_stats_prep<true><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p, q.p);
+    else k_stats_prep<false><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p, q.p);
     TV_LAUNCH();
     TV_CUDA(cudaMemsetAsync(chunks.p + N, 0, sizeof(unsigned long long), st));
     scan.exclusive(chunks.p, off.p, N + 1, st);
@@ -1240,9 +1235,6 @@ int grid_channels(GridImpl& G, const float* density, const float* temperature, c
       if (box) stats_scan<true>(L, desc.p, N, off.p, total, owner, q.p, g, sms, st);
       else stats_scan<false>(L, desc.p, N, off.p, total, owner, q.p, g, sms, st);
     }
-    if (box) k_leaf_small<true><<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g);
-    else k_leaf_small<false><<<blocks_for(N), TPB, 0, st>>>(L, N, q.p, g);
-    TV_LAUNCH();
   };
   const float* vols[3] = {temperature, albedo, aniso};
   int mask = 8;
