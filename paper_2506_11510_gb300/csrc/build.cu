@@ -13,7 +13,7 @@
 // density statistics of the new leaves are gathered by warps over chunks of
 // their voxel bounding boxes (exact integer inside tests against the four face
 // planes), then the criterion is evaluated once per new leaf.
-// Finalize: faces are matched through a hash of their vertex sums (verified
+// Finalize: faces are matched by a radix sort of their vertex sums (verified
 // against the full vertex triples), then the 32-byte records are packed.
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
@@ -44,9 +44,18 @@ struct CamD {
   double tanF, tanX, near_g, thr;
 };
 
+// The camera of criterion 2 rounded to float, with the magnitudes the error
+// bounds of the float evaluation need (see camera_allows_f32).
+struct CamF {
+  float eye[3], f[3], r[3], u[3];
+  float tanF, tanX, near_g, thr;
+  float ef, er, eu;                 // sum_a |f_a| |eye_a|, and the same for r and u
+};
+
 struct Crit {
   Geo g;
   CamD cam;
+  CamF camf;
   int var_on;
   unsigned long long theta_q16;
 };
@@ -637,6 +646,70 @@ __device__ bool camera_allows(const CamD& c, const Geo& g, const int x[4][3]) {
   return lmax2 > __dmul_rn(pix, pix);
 }
 
+// Criterion 2 in float with a bound on the error of every quantity it compares,
+// relative to the exact value of the fp64 inputs: 1 or 0 when every comparison
+// is decided by more than its bound (then the exact value, and so camera_allows,
+// whose fp64 rounding is far inside the bound, decides the same way), -1 when
+// one is too close to call (the caller then takes camera_allows).  Every float
+// operation here is rounded once (relative error 2^-24), the inputs' conversion
+// to float too; the bounds allow 2^-20, sixteen times that, on every term.
+__device__ int camera_allows_f32(const CamF& c, const Geo& g, const int x[4][3]) {
+  const float e = 9.5367431640625e-07f;           // 2^-20
+  const float s = __int_as_float((127 - g.K) << 23);   // 2^-K (K < 127)
+  float zc[4], xc[4], yc[4], ez[4], ex[4], ey[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float d[3], ad[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      d[a] = (float)x[i][a] * s - c.eye[a];       // x < 2^24: x s is exact
+      ad[a] = fabsf(d[a]);
+    }
+    zc[i] = d[0] * c.f[0] + d[1] * c.f[1] + d[2] * c.f[2];
+    xc[i] = d[0] * c.r[0] + d[1] * c.r[1] + d[2] * c.r[2];
+    yc[i] = d[0] * c.u[0] + d[1] * c.u[1] + d[2] * c.u[2];
+    ez[i] = e * (ad[0] * fabsf(c.f[0]) + ad[1] * fabsf(c.f[1]) + ad[2] * fabsf(c.f[2]) + c.ef);
+    ex[i] = e * (ad[0] * fabsf(c.r[0]) + ad[1] * fabsf(c.r[1]) + ad[2] * fabsf(c.r[2]) + c.er);
+    ey[i] = e * (ad[0] * fabsf(c.u[0]) + ad[1] * fabsf(c.u[1]) + ad[2] * fabsf(c.u[2]) + c.eu);
+  }
+  bool near_ = true, right = true, left = true, top = true, bottom = true;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float gz = zc[i] - c.near_g;
+    if (fabsf(gz) <= ez[i] + e * c.near_g) return -1;
+    near_ = near_ && gz < 0.f;
+    const float ax = zc[i] * c.tanX, ay = zc[i] * c.tanF;
+    const float bx = ex[i] + ez[i] * c.tanX + e * (fabsf(xc[i]) + fabsf(ax));
+    const float by = ey[i] + ez[i] * c.tanF + e * (fabsf(yc[i]) + fabsf(ay));
+    const float gr = xc[i] - ax, gl = xc[i] + ax, gt = yc[i] - ay, gb = yc[i] + ay;
+    if (fabsf(gr) <= bx || fabsf(gl) <= bx || fabsf(gt) <= by || fabsf(gb) <= by) return -1;
+    right = right && gr > 0.f;
+    left = left && gl < 0.f;
+    top = top && gt > 0.f;
+    bottom = bottom && gb < 0.f;
+  }
+  if (near_ || right || left || top || bottom) return 0;
+  float zmin = fminf(fminf(zc[0], zc[1]), fminf(zc[2], zc[3]));
+  float ezm = fmaxf(fmaxf(ez[0], ez[1]), fmaxf(ez[2], ez[3]));
+  if (fabsf(zmin - c.near_g) <= ezm + e * c.near_g) return -1;
+  if (zmin < c.near_g) { zmin = c.near_g; ezm = 0.f; }
+  long long L2 = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 4; ++j) {
+      long long d2 = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { const long long t = (long long)x[i][a] - x[j][a]; d2 += t * t; }
+      L2 = max(L2, d2);
+    }
+  const float lm = (float)L2 * s * s;
+  const float pix = c.thr * zmin, P = pix * pix;
+  const float gf = lm - P;
+  if (fabsf(gf) <= e * (lm + P) + 2.5f * pix * c.thr * ezm) return -1;
+  return gf > 0.f ? 1 : 0;
+}
+
 // A3 statistics, pass 3 (empty D -> voxel of the centroid) and the criterion of every new leaf
 __global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, const uint32_t* __restrict__ q,
                                Crit C, const uint8_t* known) {
@@ -665,7 +738,10 @@ __global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, c
     const unsigned __int128 rhs = (unsigned __int128)C.theta_q16 * L.sum[i];
     s = lhs > rhs;
   }
-  if (s) s = camera_allows(C.cam, g, x);
+  if (s && C.cam.on) {
+    const int f = camera_allows_f32(C.camf, g, x);
+    s = f < 0 ? camera_allows(C.cam, g, x) : f == 1;
+  }
   L.crit[i] = s ? 1 : 0;
 }
 
@@ -742,30 +818,37 @@ __global__ void k_split(LeafPtrs S, long long n, const unsigned long long* marks
 }
 
 // A6: face matching
-__device__ __forceinline__ unsigned long long face_key(const int x[4][3], int f) {
-  long long s[3] = {0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (k != f)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) s[a] += x[k][a];
-  return pack3(s[0], s[1], s[2]);
-}
-
-__global__ void k_face_insert(const int4* v, long long n, unsigned long long* keys, unsigned long long mask,
-                              uint32_t* fcnt, uint32_t* flo, uint32_t* fhi, int* err) {
+// Faces as (key, 4 i + f), the key the vertex sum of the face packed in 3 fields
+// of fb bits; sorted by key, the two faces of a shared key are neighbours.
+__global__ void k_face_keys(const int4* v, long long n, int fb, unsigned long long* keys, uint32_t* ids) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int x[4][3];
   load_tet(v, i, x);
+#pragma unroll
   for (int f = 0; f < 4; ++f) {
-    const long long s = hset_insert(keys, mask, face_key(x, f), nullptr);
-    if (s < 0) { atomicOr(err, 32); return; }
-    const uint32_t id = (uint32_t)(4 * i + f);
-    atomicAdd(fcnt + s, 1u);
-    atomicMin(flo + s, id);
-    atomicMax(fhi + s, id);
+    unsigned long long s[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k != f)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s[a] += (unsigned long long)x[k][a];
+    keys[4 * i + f] = s[0] | (s[1] << fb) | (s[2] << (2 * fb));
+    ids[4 * i + f] = (uint32_t)(4 * i + f);
   }
+}
+
+// The face across each face (4 i' + f'), or NO_FACE for a face of one cell;
+// three faces with one key flag the grid.
+constexpr uint32_t NO_FACE = 0xFFFFFFFFu;
+__global__ void k_face_pairs(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ ids,
+                             long long nf, uint32_t* nbr, int* err) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nf) return;
+  const unsigned long long k = keys[p];
+  const bool prev = p > 0 && keys[p - 1] == k, next = p + 1 < nf && keys[p + 1] == k;
+  if (prev && next) atomicOr(err, 8);
+  nbr[ids[p]] = next ? ids[p + 1] : (prev ? ids[p - 1] : NO_FACE);
 }
 
 __device__ __forceinline__ bool same_face(const int x[4][3], int f, const int y[4][3], int g) {
@@ -790,9 +873,8 @@ __device__ __forceinline__ uint32_t encode_density(double mean, int fmt) {
   return __float_as_uint(f);
 }
 
-__global__ void k_finalize(LeafPtrs L, long long n, Geo g, int fmt, const unsigned long long* keys,
-                           unsigned long long mask, const uint32_t* fcnt, const uint32_t* flo, const uint32_t* fhi,
-                           uint4* rec, float* majorant, int* err) {
+__global__ void k_finalize(LeafPtrs L, long long n, Geo g, int fmt, const uint32_t* __restrict__ fnbr, uint4* rec,
+                           float* majorant, int* err) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int x[4][3];
@@ -800,18 +882,14 @@ __global__ void k_finalize(LeafPtrs L, long long n, Geo g, int fmt, const unsign
   uint32_t link[4];
   int cpl[4];
   for (int f = 0; f < 4; ++f) {
-    const long long s = hset_find(keys, mask, face_key(x, f));
     uint32_t nb = NO_NBR;
-    if (s < 0) { atomicOr(err, 1); return; }
-    const uint32_t c = fcnt[s];
-    const uint32_t me = (uint32_t)(4 * i + f);
-    if (c == 2) {
-      const uint32_t other = flo[s] == me ? fhi[s] : flo[s];
+    const uint32_t other = fnbr[4 * i + f];
+    if (other != NO_FACE) {
       int y[4][3];
       load_tet(L.v, other >> 2, y);
       if (!same_face(x, f, y, (int)(other & 3))) { atomicOr(err, 2); return; }
       nb = other >> 2;
-    } else if (c == 1) {
+    } else {
       // a face of one cell must lie on the domain boundary
       bool bnd = false;
       const int a = (f + 1) & 3, b = (f + 2) & 3, cc = (f + 3) & 3;
@@ -821,9 +899,6 @@ __global__ void k_finalize(LeafPtrs L, long long n, Geo g, int fmt, const unsign
         if (x[a][ax] == x[b][ax] && x[a][ax] == x[cc][ax] && (x[a][ax] == 0 || x[a][ax] == lim)) bnd = true;
       }
       if (!bnd) { atomicOr(err, 4); return; }
-    } else {
-      atomicOr(err, 8);
-      return;
     }
     int nrm[3];
     long long rhs;
@@ -968,6 +1043,19 @@ CamD camera_for_criterion(const tg_camera* cam, float footprint_px, const float 
   return c;
 }
 
+CamF camera_f32(const CamD& c) {
+  CamF f;
+  std::memset(&f, 0, sizeof f);
+  for (int a = 0; a < 3; ++a) {
+    f.eye[a] = (float)c.eye[a]; f.f[a] = (float)c.f[a]; f.r[a] = (float)c.r[a]; f.u[a] = (float)c.u[a];
+    f.ef += std::fabs(f.f[a]) * std::fabs(f.eye[a]);
+    f.er += std::fabs(f.r[a]) * std::fabs(f.eye[a]);
+    f.eu += std::fabs(f.u[a]) * std::fabs(f.eye[a]);
+  }
+  f.tanF = (float)c.tanF; f.tanX = (float)c.tanX; f.near_g = (float)c.near_g; f.thr = (float)c.thr;
+  return f;
+}
+
 }  // namespace
 
 int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera* cam, float footprint_px,
@@ -990,6 +1078,7 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   C.g = g;
   const double cube = (double)vol->voxel_size * (double)n;
   C.cam = camera_for_criterion(cam, footprint_px, vol->box_min, cube);
+  C.camf = camera_f32(C.cam);
   C.var_on = theta >= 0.f;
   C.theta_q16 = C.var_on ? (unsigned long long)std::llround((double)theta * 65536.0) : 0ull;
 
@@ -1118,21 +1207,29 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   acode.alloc(0); asum.alloc(0); acnt.alloc(0); amn.alloc(0); amx.alloc(0);
 
   // ---- finalize: neighbours, orientations, planes, densities, records ----
-  const unsigned long long fcap = next_pow2(std::max<long long>(1024, 4 * N));
-  DevBuf<unsigned long long> fkeys(fcap);
-  DevBuf<uint32_t> fcnt(fcap), flo(fcap), fhi(fcap);
-  TV_CUDA(cudaMemsetAsync(fkeys.p, 0xFF, fcap * 8, st));
-  TV_CUDA(cudaMemsetAsync(fcnt.p, 0, fcap * 4, st));
-  TV_CUDA(cudaMemsetAsync(flo.p, 0xFF, fcap * 4, st));
-  TV_CUDA(cudaMemsetAsync(fhi.p, 0, fcap * 4, st));
+  const long long NF = 4 * N;
+  DevBuf<uint32_t> fnbr(NF);
   DevBuf<uint4> rec(2 * N);
   DevBuf<float> maj(N);
   DevBuf<int> err(2);
   TV_CUDA(cudaMemsetAsync(err.p, 0, 8, st));
-  k_face_insert<<<blocks_for(N), TPB, 0, st>>>(A.v.p, N, fkeys.p, fcap - 1, fcnt.p, flo.p, fhi.p, err.p);
-  TV_LAUNCH();
-  k_finalize<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, g, fmt, fkeys.p, fcap - 1, fcnt.p, flo.p, fhi.p, rec.p,
-                                            maj.p, err.p);
+  {
+    // face keys: vertex sums below 3 C 2^K per axis
+    int fb = 1;
+    for (int a = 0; a < 3; ++a)
+      while ((1ll << fb) <= 3ll * ((long long)g.C[a] << g.K)) ++fb;
+    DevBuf<unsigned long long> fk(NF), fks(NF);
+    DevBuf<uint32_t> fid(NF), fids(NF);
+    k_face_keys<<<blocks_for(N), TPB, 0, st>>>(A.v.p, N, fb, fk.p, fid.p);
+    TV_LAUNCH();
+    size_t bytes = 0;
+    TV_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, fk.p, fks.p, fid.p, fids.p, NF, 0, 3 * fb, st));
+    DevBuf<char> tmp(bytes + 16);
+    TV_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, bytes, fk.p, fks.p, fid.p, fids.p, NF, 0, 3 * fb, st));
+    k_face_pairs<<<blocks_for(NF), TPB, 0, st>>>(fks.p, fids.p, NF, fnbr.p, err.p);
+    TV_LAUNCH();
+  }
+  k_finalize<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, g, fmt, fnbr.p, rec.p, maj.p, err.p);
   TV_LAUNCH();
   int herr = 0;
   TV_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
