@@ -1,15 +1,18 @@
 // leb_build: the adaptive conforming grid of Sec. 2 on the GPU.
 //
-// Leaves live in structure-of-arrays form and are rebuilt every round by a
-// stable compaction in which a split leaf is replaced, in place, by its two
-// children (bit 0 then bit 1).  Starting from the roots in code order this
-// keeps the leaves in depth-first order of their LEB codes at every round, so
-// the final grid needs no sort.
+// Leaves live in structure-of-arrays form.  While many of them split, each
+// round rebuilds them by a stable compaction in which a split leaf is replaced,
+// in place, by its two children (bit 0 then bit 1); starting from the roots in
+// code order this keeps them in depth-first order of their LEB codes.  Once few
+// split (the closure's last rounds), the first child takes its parent's slot
+// and the second is appended, so a round touches only what it splits; after
+// the last round the appended run is sorted and merged with the ordered one.
 //
 // Round: (1) mark = criterion || hanging vertex (one of the six edge
 // midpoints is a vertex of the grid, found in an open-addressing hash set of
-// packed vertex coordinates); (2) exclusive scan of the marks gives every leaf
-// its output slot; (3) split / copy, inserting the new vertices; (4) the
+// packed vertex coordinates; leaves checked in an earlier round look only at
+// the vertices the last split added); (2) exclusive scan of the marks gives
+// every split leaf its rank; (3) split, inserting the new vertices; (4) the
 // density statistics of the new leaves are gathered by warps over chunks of
 // their voxel bounding boxes (exact integer inside tests against the four face
 // planes), then the criterion is evaluated once per new leaf.
@@ -89,8 +92,30 @@ struct Leaves {
     v.alloc(3 * c); code.alloc(c); sum.alloc(c); tag.alloc(c); crit.alloc(c); cnt.alloc(c); mn.alloc(c); mx.alloc(c);
     cap = c;
   }
+  // room for n leaves, keeping the first `used` (geometric growth)
+  void grow(size_t n, size_t used, cudaStream_t st) {
+    if (n <= cap) return;
+    Leaves g;
+    g.ensure(n);
+    if (used) {
+      TV_CUDA(cudaMemcpyAsync(g.v.p, v.p, used * 3 * sizeof(int4), cudaMemcpyDeviceToDevice, st));
+      TV_CUDA(cudaMemcpyAsync(g.code.p, code.p, used * 8, cudaMemcpyDeviceToDevice, st));
+      TV_CUDA(cudaMemcpyAsync(g.sum.p, sum.p, used * 8, cudaMemcpyDeviceToDevice, st));
+      TV_CUDA(cudaMemcpyAsync(g.tag.p, tag.p, used, cudaMemcpyDeviceToDevice, st));
+      TV_CUDA(cudaMemcpyAsync(g.crit.p, crit.p, used, cudaMemcpyDeviceToDevice, st));
+      TV_CUDA(cudaMemcpyAsync(g.cnt.p, cnt.p, used * 4, cudaMemcpyDeviceToDevice, st));
+      TV_CUDA(cudaMemcpyAsync(g.mn.p, mn.p, used * 4, cudaMemcpyDeviceToDevice, st));
+      TV_CUDA(cudaMemcpyAsync(g.mx.p, mx.p, used * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    *this = std::move(g);            // the old arrays are given back on the stream, after the copies
+  }
   LeafPtrs ptrs() { return LeafPtrs{v.p, code.p, tag.p, cnt.p, mn.p, mx.p, sum.p, crit.p}; }
 };
+
+// crit of a leaf: the criterion asks for its split; it is new (created by the
+// last split, or a root), its edges not yet checked against the vertex set; or
+// it is an older leaf whose edges were checked when the set was smaller
+constexpr uint8_t CRIT_OLD = 0, CRIT_SPLIT = 1, CRIT_NEW = 2;
 
 __device__ __forceinline__ unsigned long long mix(unsigned long long k) {
   k ^= k >> 31; k *= 0x7FB5D329728EA185ull;
@@ -742,79 +767,147 @@ __global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, c
     const int f = camera_allows_f32(C.camf, g, x);
     s = f < 0 ? camera_allows(C.cam, g, x) : f == 1;
   }
-  L.crit[i] = s ? 1 : 0;
+  L.crit[i] = s ? CRIT_SPLIT : CRIT_NEW;
 }
 
-// A5: mark = criterion || a vertex of the grid at one of the six edge midpoints
+// A5: mark = criterion || a vertex of the grid at one of the six edge midpoints.
+// Vertices are only ever added, and a leaf that was checked in an earlier round
+// had none at its midpoints then, so an older leaf is checked against the
+// vertices the last split added (dkeys, a small set) and only a new leaf
+// against the whole set; the marks are those of checking every leaf against
+// every vertex.
 __global__ void k_mark(LeafPtrs L, long long n, const unsigned long long* keys, unsigned long long mask,
-                       unsigned long long* marks, unsigned long long* nmark) {
+                       const unsigned long long* dkeys, unsigned long long dmask, unsigned long long* marks,
+                       unsigned long long* nmark) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool mk = false;
   if (i < n) {
-    mk = L.crit[i] != 0;
-    if (!mk) {
+    const uint8_t c = L.crit[i];
+    mk = c == CRIT_SPLIT;
+    if (!mk && (c == CRIT_NEW || dkeys)) {
+      const unsigned long long* K = c == CRIT_NEW ? keys : dkeys;
+      const unsigned long long km = c == CRIT_NEW ? mask : dmask;
       int x[4][3];
       load_tet(L.v, i, x);
       for (int a = 0; a < 4 && !mk; ++a)
         for (int b = a + 1; b < 4 && !mk; ++b) {
           const int s0 = x[a][0] + x[b][0], s1 = x[a][1] + x[b][1], s2 = x[a][2] + x[b][2];
           if ((s0 | s1 | s2) & 1) continue;        // off the lattice: not a vertex
-          mk = hset_find(keys, mask, pack3(s0 >> 1, s1 >> 1, s2 >> 1)) >= 0;
+          mk = hset_find(K, km, pack3(s0 >> 1, s1 >> 1, s2 >> 1)) >= 0;
         }
     }
+    if (c == CRIT_NEW && !mk) L.crit[i] = CRIT_OLD;
     marks[i] = mk ? 1 : 0;
   }
   const unsigned b = __ballot_sync(~0u, mk);
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(nmark, (unsigned long long)__popc(b));
 }
 
-// A4: Maubach bisection of the marked leaves, copy of the others, stable order
+// The two children of leaf i (Maubach bisection of its refinement edge x0 xk);
+// returns the new vertex.
+__device__ __forceinline__ void bisect(const int x[4][3], int k, int w, int y[4][3]) {
+  int o = 0;
+  for (int s = w; s < k + w; ++s, ++o)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) y[o][a] = x[s][a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) y[o][a] = (x[0][a] + x[k][a]) >> 1;
+  ++o;
+  for (int s = k + 1; s < 4; ++s, ++o)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) y[o][a] = x[s][a];
+}
+
+// A4: Maubach bisection of the marked leaves.  While many leaves split, the
+// leaves are rebuilt by a stable compaction in which a split leaf is replaced
+// by its two children, which keeps them in depth-first order of their codes
+// (APPEND false).  Once few do, the first child takes its parent's slot and the
+// second is appended at n + its parent's rank among the split leaves, so a round
+// touches only the leaves it splits (APPEND true; the appended leaves are put
+// in order after the last round).  The new vertices go to the vertex set and
+// to this round's set dkeys.
+template <bool APPEND>
 __global__ void k_split(LeafPtrs S, long long n, const unsigned long long* marks, const unsigned long long* pos,
                         LeafPtrs D, long long* newlist, unsigned long long* keys, unsigned long long mask,
-                        unsigned long long* vcount, NodePtrs arch, long long abase) {
+                        unsigned long long* dkeys, unsigned long long dmask, unsigned long long* vcount,
+                        NodePtrs arch, long long abase) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const long long before = (long long)pos[i];
-  const long long j = i + before;
   if (!marks[i]) {
+    if (APPEND) return;
+    const long long j = i + before;
     D.v[3 * j] = S.v[3 * i]; D.v[3 * j + 1] = S.v[3 * i + 1]; D.v[3 * j + 2] = S.v[3 * i + 2];
     D.code[j] = S.code[i]; D.tag[j] = S.tag[i]; D.crit[j] = S.crit[i];
     D.cnt[j] = S.cnt[i]; D.sum[j] = S.sum[i]; D.mn[j] = S.mn[i]; D.mx[j] = S.mx[i];
     return;
   }
+  const unsigned long long code = S.code[i];
   {
     const long long a = abase + before;
-    arch.code[a] = S.code[i]; arch.sum[a] = S.sum[i];
+    arch.code[a] = code; arch.sum[a] = S.sum[i];
     arch.cnt[a] = S.cnt[i]; arch.mn[a] = S.mn[i]; arch.mx[a] = S.mx[i];
   }
   int x[4][3];
   load_tet(S.v, i, x);
   const int k = S.tag[i];
-  int z[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) z[a] = (x[0][a] + x[k][a]) >> 1;
-  const unsigned long long code = S.code[i];
   const int depth = (int)(code & 63ull);
   const unsigned long long base = (code & ~63ull) | (unsigned long long)(depth + 1);
   const uint8_t nt = (uint8_t)(k > 1 ? k - 1 : 3);
+#pragma unroll
   for (int w = 0; w < 2; ++w) {
     int y[4][3];
-    int o = 0;
-    for (int s = w; s < k + w; ++s, ++o)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) y[o][a] = x[s][a];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) y[o][a] = z[a];
-    ++o;
-    for (int s = k + 1; s < 4; ++s, ++o)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) y[o][a] = x[s][a];
-    store_tet(D.v, j + w, y);
-    D.code[j + w] = base | ((unsigned long long)w << (55 - depth));
-    D.tag[j + w] = nt;
-    newlist[2 * before + w] = j + w;
+    bisect(x, k, w, y);
+    const long long j = APPEND ? (w == 0 ? i : n + before) : i + before + w;
+    store_tet(D.v, j, y);
+    D.code[j] = base | ((unsigned long long)w << (55 - depth));
+    D.tag[j] = nt;
+    newlist[2 * before + w] = j;
   }
-  if (hset_insert(keys, mask, pack3(z[0], z[1], z[2]), vcount) < 0) atomicAdd(vcount + 3, 1ull);
+  const unsigned long long key = pack3((x[0][0] + x[k][0]) >> 1, (x[0][1] + x[k][1]) >> 1, (x[0][2] + x[k][2]) >> 1);
+  if (hset_insert(keys, mask, key, vcount) < 0) atomicAdd(vcount + 3, 1ull);
+  if (hset_insert(dkeys, dmask, key, nullptr) < 0) atomicAdd(vcount + 3, 1ull);
+}
+
+// number of the n sorted codes a[] below c
+__device__ __forceinline__ long long count_below(const unsigned long long* __restrict__ a, long long n,
+                                                 unsigned long long c) {
+  long long lo = 0, hi = n;
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if (a[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// The leaves in code order, into the arrays the grid keeps: leaves [0, ns) are in
+// order already, the nt appended after them are in order through tperm (their
+// codes sorted: tcode), and each leaf's place is its rank in its own run plus the
+// number of the other run's codes below its own.
+__global__ void k_place_leaves(LeafPtrs S, long long ns, long long nt, const unsigned long long* __restrict__ tcode,
+                               const uint32_t* __restrict__ tperm, LeafPtrs D) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns + nt) return;
+  long long src, dst;
+  unsigned long long code;
+  if (t < ns) {
+    src = t;
+    code = S.code[t];
+    dst = t + count_below(tcode, nt, code);
+  } else {
+    const long long r = t - ns;
+    src = ns + tperm[r];
+    code = tcode[r];
+    dst = r + count_below(S.code, ns, code);
+  }
+  D.v[3 * dst] = S.v[3 * src]; D.v[3 * dst + 1] = S.v[3 * src + 1]; D.v[3 * dst + 2] = S.v[3 * src + 2];
+  D.code[dst] = code; D.tag[dst] = S.tag[src];
+  D.cnt[dst] = S.cnt[src]; D.sum[dst] = S.sum[src]; D.mn[dst] = S.mn[src]; D.mx[dst] = S.mx[src];
+}
+
+__global__ void k_iota32(uint32_t* a, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (uint32_t)i;
 }
 
 // A6: face matching
@@ -1120,10 +1213,12 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   LookupBufs lk;
 
   Scanner scan;
-  DevBuf<unsigned long long> chunks, off, marks, pos;
+  DevBuf<unsigned long long> chunks, off, marks, pos, dkeys;
+  unsigned long long dcap = 0;                     // the last split's vertices (none before the first)
   DevBuf<int> owner;
   DevBuf<ScanDesc> desc;
   DevBuf<long long> newlist;
+  long long nsorted = -1;                          // leaves [0, nsorted) in code order once splits append
   // interior nodes, appended as leaves are split
   DevBuf<unsigned long long> acode, asum;
   DevBuf<uint32_t> acnt, amn, amx;
@@ -1137,7 +1232,8 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     marks.ensure(N + 1);
     pos.ensure(N + 1);
     TV_CUDA(cudaMemsetAsync(counters.p + 1, 0, 8, st));
-    k_mark<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, hkeys.p, hcap - 1, marks.p, counters.p + 1);
+    k_mark<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, hkeys.p, hcap - 1, dcap ? dkeys.p : nullptr, dcap - 1,
+                                          marks.p, counters.p + 1);
     TV_LAUNCH();
     unsigned long long hc[4];
     TV_CUDA(cudaMemcpyAsync(hc, counters.p, 32, cudaMemcpyDeviceToHost, st));
@@ -1161,8 +1257,18 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     }
     TV_CUDA(cudaMemsetAsync(marks.p + N, 0, 8, st));
     scan.exclusive(marks.p, pos.p, N + 1, st);
-    B.ensure(N + M);
+    // splits append once fewer than one leaf in eight splits (the compaction would copy every leaf)
+    if (nsorted < 0 && 8 * M < N) {
+      nsorted = N;
+      B = Leaves();
+    }
+    if (nsorted >= 0) A.grow(N + M, N, st);
+    else B.ensure(N + M);
     newlist.ensure(2 * M);
+    // this split's vertices (at most one per split leaf: the set stays under a quarter full)
+    dcap = next_pow2(std::max<long long>(1024, 4 * M));
+    dkeys.ensure(dcap);
+    TV_CUDA(cudaMemsetAsync(dkeys.p, 0xFF, dcap * 8, st));
     if ((size_t)(nint + M) > acode.n) {
       // grow the interior-node arrays (keep what they hold)
       const size_t cap = std::max<size_t>(2 * (size_t)(nint + M), 1024);
@@ -1179,14 +1285,47 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
       acode = std::move(c2); asum = std::move(s2); acnt = std::move(n2); amn = std::move(m2); amx = std::move(x2);
     }
     const NodePtrs arch{acode.p, asum.p, acnt.p, amn.p, amx.p};
-    k_split<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, marks.p, pos.p, B.ptrs(), newlist.p, hkeys.p, hcap - 1,
-                                           counters.p, arch, nint);
-    TV_LAUNCH();
-    std::swap(A, B);
+    if (nsorted >= 0) {
+      k_split<true><<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, marks.p, pos.p, A.ptrs(), newlist.p, hkeys.p,
+                                                   hcap - 1, dkeys.p, dcap - 1, counters.p, arch, nint);
+      TV_LAUNCH();
+    } else {
+      k_split<false><<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, marks.p, pos.p, B.ptrs(), newlist.p, hkeys.p,
+                                                    hcap - 1, dkeys.p, dcap - 1, counters.p, arch, nint);
+      TV_LAUNCH();
+      std::swap(A, B);
+    }
     N += M;
     nint += M;
     stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, owner, desc, st, sms, pp, lk);
   }
+
+  dkeys.alloc(0); marks.alloc(0); pos.alloc(0); newlist.alloc(0); chunks.alloc(0); off.alloc(0); owner.alloc(0);
+  desc.alloc(0); B = Leaves();
+
+  // ---- the leaves in code order, in exact-size arrays ----
+  DevBuf<unsigned long long> codes(N), sum(N), scratch(4);
+  DevBuf<int4> verts(3 * N);
+  DevBuf<uint8_t> tag(N);
+  DevBuf<uint32_t> cnt(N), mn(N), mx(N);
+  {
+    const long long ns = nsorted < 0 ? N : nsorted, nt = N - ns;
+    DevBuf<unsigned long long> tcode(nt > 0 ? nt : 1);
+    DevBuf<uint32_t> tiota(nt > 0 ? nt : 1), tperm(nt > 0 ? nt : 1);
+    if (nt > 0) {
+      k_iota32<<<blocks_for(nt), TPB, 0, st>>>(tiota.p, nt);
+      TV_LAUNCH();
+      size_t bytes = 0;
+      TV_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, A.code.p + ns, tcode.p, tiota.p, tperm.p, nt, 0, 64, st));
+      DevBuf<char> tmp(bytes + 16);
+      TV_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, bytes, A.code.p + ns, tcode.p, tiota.p, tperm.p, nt, 0, 64, st));
+    }
+    const LeafPtrs D{verts.p, codes.p, tag.p, cnt.p, mn.p, mx.p, sum.p, nullptr};
+    k_place_leaves<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), ns, nt, tcode.p, tperm.p, D);
+    TV_LAUNCH();
+  }
+  A = Leaves();
+  const LeafPtrs F{verts.p, codes.p, tag.p, cnt.p, mn.p, mx.p, sum.p, nullptr};
 
   // ---- interior-node statistics sorted by code (for rebuilds) ----
   DevBuf<unsigned long long> ncode(nint > 0 ? nint : 1), nsum(nint > 0 ? nint : 1);
@@ -1220,7 +1359,7 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
       while ((1ll << fb) <= 3ll * ((long long)g.C[a] << g.K)) ++fb;
     DevBuf<unsigned long long> fk(NF), fks(NF);
     DevBuf<uint32_t> fid(NF), fids(NF);
-    k_face_keys<<<blocks_for(N), TPB, 0, st>>>(A.v.p, N, fb, fk.p, fid.p);
+    k_face_keys<<<blocks_for(N), TPB, 0, st>>>(F.v, N, fb, fk.p, fid.p);
     TV_LAUNCH();
     size_t bytes = 0;
     TV_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, fk.p, fks.p, fid.p, fids.p, NF, 0, 3 * fb, st));
@@ -1229,25 +1368,13 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     k_face_pairs<<<blocks_for(NF), TPB, 0, st>>>(fks.p, fids.p, NF, fnbr.p, err.p);
     TV_LAUNCH();
   }
-  k_finalize<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, g, fmt, fnbr.p, rec.p, maj.p, err.p);
+  k_finalize<<<blocks_for(N), TPB, 0, st>>>(F, N, g, fmt, fnbr.p, rec.p, maj.p, err.p);
   TV_LAUNCH();
   int herr = 0;
   TV_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
   TV_CUDA(cudaStreamSynchronize(st));
   if (herr) return TG_EGRID;
 
-  // exact-size copies of the arrays the grid keeps
-  DevBuf<unsigned long long> codes(N), sum(N), scratch(4);
-  DevBuf<int4> verts(3 * N);
-  DevBuf<uint8_t> tag(N);
-  DevBuf<uint32_t> cnt(N), mn(N), mx(N);
-  TV_CUDA(cudaMemcpyAsync(codes.p, A.code.p, N * 8, cudaMemcpyDeviceToDevice, st));
-  TV_CUDA(cudaMemcpyAsync(sum.p, A.sum.p, N * 8, cudaMemcpyDeviceToDevice, st));
-  TV_CUDA(cudaMemcpyAsync(verts.p, A.v.p, N * 48, cudaMemcpyDeviceToDevice, st));
-  TV_CUDA(cudaMemcpyAsync(tag.p, A.tag.p, N, cudaMemcpyDeviceToDevice, st));
-  TV_CUDA(cudaMemcpyAsync(cnt.p, A.cnt.p, N * 4, cudaMemcpyDeviceToDevice, st));
-  TV_CUDA(cudaMemcpyAsync(mn.p, A.mn.p, N * 4, cudaMemcpyDeviceToDevice, st));
-  TV_CUDA(cudaMemcpyAsync(mx.p, A.mx.p, N * 4, cudaMemcpyDeviceToDevice, st));
   TV_CUDA(cudaMemsetAsync(scratch.p, 0, 32, st));
   int depth_reached = 0;
   TV_CUDA(cudaMemsetAsync(err.p + 1, 0, 4, st));

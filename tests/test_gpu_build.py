@@ -86,6 +86,26 @@ def test_build_edge_cases(case):
     CK.check_grid(ref)
 
 
+@pytest.mark.parametrize("k", range(4))
+def test_build_camera_criterion_random_views(k):
+    """Criterion 2 alone (the density criterion off) for seeded random views -- eyes
+    inside and outside the box, frustum edges and the near plane across it: the
+    kernel's float decisions, and its fp64 evaluation where a comparison is too
+    close to call in float, give the oracle's grid."""
+    import paper_2506_11510_gb300 as tv
+    rng = np.random.default_rng(300 + k)
+    vol = scene_volume("adaptive_small")
+    eye = tuple(float(v) for v in rng.uniform(-0.5, 1.5, 3))
+    target = tuple(float(v) for v in rng.uniform(0.2, 0.8, 3))
+    s = W.with_camera(W.scene("adaptive_small", variation_threshold=-1.0, footprint_px=float(rng.uniform(0.5, 3.0)),
+                              max_depth=18),
+                      pos=eye, target=target, fov_y_deg=float(rng.uniform(20.0, 80.0)))
+    grid = tv.build_scene_grid(s, torch.from_numpy(vol).cuda())
+    ref = O.Grid.for_scene(s, vol).export()
+    assert len(ref.codes) > 24
+    assert_same_grid(gpu_arrays(grid), ref)
+
+
 def test_build_rejects_bad_arguments():
     import paper_2506_11510_gb300 as tv
     vol = torch.zeros((16, 16, 16), device="cuda")
