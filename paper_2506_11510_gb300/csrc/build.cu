@@ -462,7 +462,7 @@ __device__ __forceinline__ void row_tail(const uint32_t* __restrict__ row, int a
 // only the voxels inside are read: by the whole warp along the rows when the box
 // is at least 32 voxels wide (coalesced; the first 32 voxels of four rows are
 // loaded together), else by each lane along its row.
-template <bool BOX>
+template <bool BOX, bool QUAD>
 __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const ScanDesc* __restrict__ desc,
                                                     const unsigned long long* chunk_off, const int* __restrict__ owner,
                                                     unsigned long long total, const uint32_t* __restrict__ q, Geo g) {
@@ -498,7 +498,43 @@ __global__ void __launch_bounds__(TPB) k_stats_scan(LeafPtrs L, const ScanDesc* 
       else row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
       rowoff = ((long long)kk * g.ny + jj) * g.nx;
     }
-    if (hi[0] - lo[0] >= 31) {
+    if (QUAD) {
+      // (rows start on 16-byte boundaries) the chunk's voxels as aligned 16-byte quads, dealt
+      // to the lanes in row order: neighbouring lanes read neighbouring quads of a row and
+      // every lane has work however long or short the rows are
+      const unsigned full = ~0u;
+      const int qa = xa >> 2;
+      const int nq = xb >= xa ? (xb >> 2) - qa + 1 : 0;
+      int incl = nq;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(full, incl, o);
+        if ((int)lane >= o) incl += t;
+      }
+      const int Q = __shfl_sync(full, incl, 31);
+      const int start = incl - nq;
+#pragma unroll 2
+      for (int g0 = 0; g0 < Q; g0 += 32) {
+        const int gq = g0 + (int)lane;
+        // the row of quad gq: the last lane whose first quad is at or before it
+        int rr = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1)
+          if (__shfl_sync(full, start, rr + step) <= gq) rr += step;
+        const int ra = __shfl_sync(full, xa, rr), rb = __shfl_sync(full, xb, rr);
+        const long long ro = __shfl_sync(full, rowoff, rr);
+        const int quad = (ra >> 2) + (gq - __shfl_sync(full, start, rr));
+        if (gq < Q) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(q + ro) + quad);
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int xx = 4 * quad + e;
+            if (xx >= ra && xx <= rb) { ++cnt; sum += w[e]; mn = min(mn, w[e]); mx = max(mx, w[e]); }
+          }
+        }
+      }
+    } else if (hi[0] - lo[0] >= 31) {
       // wide box: lanes along x (coalesced), four rows at a time
       for (int k = 0; k < 32; k += 4) {
         int a[4], b[4];
@@ -1044,7 +1080,11 @@ void stats_scan(LeafPtrs L, const ScanDesc* desc, long long m, const unsigned lo
   k_chunk_owner<<<blocks_for(m), TPB, 0, st>>>(off, m, owner.p);
   TV_LAUNCH();
   const long long wblocks = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
-  k_stats_scan<BOX><<<(unsigned)wblocks, TPB, 0, st>>>(L, desc, off, owner.p, total, q, g);
+  // 16-byte loads along the rows when every row starts on a 16-byte boundary
+  if (g.nx % 4 == 0 && reinterpret_cast<uintptr_t>(q) % 16 == 0)
+    k_stats_scan<BOX, true><<<(unsigned)wblocks, TPB, 0, st>>>(L, desc, off, owner.p, total, q, g);
+  else
+    k_stats_scan<BOX, false><<<(unsigned)wblocks, TPB, 0, st>>>(L, desc, off, owner.p, total, q, g);
   TV_LAUNCH();
 }
 
