@@ -10,8 +10,7 @@
 //
 // Round: (1) mark = criterion || hanging vertex (one of the six edge
 // midpoints is a vertex of the grid, found in an open-addressing hash set of
-// packed vertex coordinates; leaves checked in an earlier round look only at
-// the vertices the last split added); (2) exclusive scan of the marks gives
+// packed vertex coordinates, behind a Bloom filter that stays in L2); (2) exclusive scan of the marks gives
 // every split leaf its rank; (3) split, inserting the new vertices; (4) the
 // density statistics of the new leaves are gathered by warps over chunks of
 // their voxel bounding boxes (exact integer inside tests against the four face
@@ -112,10 +111,6 @@ struct Leaves {
   LeafPtrs ptrs() { return LeafPtrs{v.p, code.p, tag.p, cnt.p, mn.p, mx.p, sum.p, crit.p}; }
 };
 
-// crit of a leaf: the criterion asks for its split; it is new (created by the
-// last split, or a root), its edges not yet checked against the vertex set; or
-// it is an older leaf whose edges were checked when the set was smaller
-constexpr uint8_t CRIT_OLD = 0, CRIT_SPLIT = 1, CRIT_NEW = 2;
 
 __device__ __forceinline__ unsigned long long mix(unsigned long long k) {
   k ^= k >> 31; k *= 0x7FB5D329728EA185ull;
@@ -153,6 +148,33 @@ __device__ __forceinline__ long long hset_find(const unsigned long long* keys, u
     s = (s + 1) & mask;
   }
   return -1;
+}
+
+// A blocked Bloom filter over the vertex set (two bits of one 32-bit word per
+// key, the word and bits from the key's hash): a clear bit proves a key absent
+// with one read of a filter small enough to stay in L2; a set pair is confirmed
+// in the hash set.
+struct Bloom {
+  uint32_t* w;
+  unsigned long long mask;          // words - 1 (a power of two)
+};
+__device__ __forceinline__ void bloom_bits(const Bloom& b, unsigned long long key, unsigned long long* word,
+                                           uint32_t* bits) {
+  const unsigned long long h = mix(key ^ 0x9E3779B97F4A7C15ull);
+  *word = h & b.mask;
+  *bits = (1u << ((h >> 40) & 31u)) | (1u << ((h >> 45) & 31u));
+}
+__device__ __forceinline__ void bloom_add(const Bloom& b, unsigned long long key) {
+  unsigned long long w;
+  uint32_t m;
+  bloom_bits(b, key, &w, &m);
+  atomicOr(b.w + w, m);
+}
+__device__ __forceinline__ bool bloom_may_hold(const Bloom& b, unsigned long long key) {
+  unsigned long long w;
+  uint32_t m;
+  bloom_bits(b, key, &w, &m);
+  return (__ldg(b.w + w) & m) == m;
 }
 
 __device__ __forceinline__ void load_tet(const int4* v, long long i, int x[4][3]) {
@@ -272,21 +294,27 @@ __global__ void k_roots(LeafPtrs L, Geo g, int nroots) {
 }
 
 __global__ void k_insert_vertices(const int4* v, long long n, unsigned long long* keys, unsigned long long mask,
-                                  unsigned long long* count) {
+                                  Bloom bloom, unsigned long long* count) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int x[4][3];
   load_tet(v, i, x);
-  for (int k = 0; k < 4; ++k)
-    if (hset_insert(keys, mask, pack3(x[k][0], x[k][1], x[k][2]), count) < 0) atomicAdd(count + 3, 1ull);
+  for (int k = 0; k < 4; ++k) {
+    const unsigned long long key = pack3(x[k][0], x[k][1], x[k][2]);
+    if (hset_insert(keys, mask, key, count) < 0) atomicAdd(count + 3, 1ull);
+    bloom_add(bloom, key);
+  }
 }
 
+// the vertex set into a larger table, and its filter into a larger filter
 __global__ void k_rehash(const unsigned long long* old, long long oldcap, unsigned long long* keys,
-                         unsigned long long mask, unsigned long long* fail) {
+                         unsigned long long mask, Bloom bloom, unsigned long long* fail) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= oldcap) return;
   const unsigned long long k = old[i];
-  if (k != EMPTY && hset_insert(keys, mask, k, nullptr) < 0) atomicAdd(fail, 1ull);
+  if (k == EMPTY) return;
+  if (hset_insert(keys, mask, k, nullptr) < 0) atomicAdd(fail, 1ull);
+  bloom_add(bloom, k);
 }
 
 // voxel index range of the centres inside [lo, hi] (units of 2^-K) along one axis
@@ -803,36 +831,29 @@ __global__ void k_stats_finish(LeafPtrs L, const long long* list, long long m, c
     const int f = camera_allows_f32(C.camf, g, x);
     s = f < 0 ? camera_allows(C.cam, g, x) : f == 1;
   }
-  L.crit[i] = s ? CRIT_SPLIT : CRIT_NEW;
+  L.crit[i] = s ? 1 : 0;
 }
 
-// A5: mark = criterion || a vertex of the grid at one of the six edge midpoints.
-// Vertices are only ever added, and a leaf that was checked in an earlier round
-// had none at its midpoints then, so an older leaf is checked against the
-// vertices the last split added (dkeys, a small set) and only a new leaf
-// against the whole set; the marks are those of checking every leaf against
-// every vertex.
-__global__ void k_mark(LeafPtrs L, long long n, const unsigned long long* keys, unsigned long long mask,
-                       const unsigned long long* dkeys, unsigned long long dmask, unsigned long long* marks,
-                       unsigned long long* nmark) {
+// A5: mark = criterion || a vertex of the grid at one of the six edge midpoints
+// (the filter rules out most midpoints with one read from L2; the rest are
+// looked up in the vertex set)
+__global__ void k_mark(LeafPtrs L, long long n, const unsigned long long* keys, unsigned long long mask, Bloom bloom,
+                       unsigned long long* marks, unsigned long long* nmark) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool mk = false;
   if (i < n) {
-    const uint8_t c = L.crit[i];
-    mk = c == CRIT_SPLIT;
-    if (!mk && (c == CRIT_NEW || dkeys)) {
-      const unsigned long long* K = c == CRIT_NEW ? keys : dkeys;
-      const unsigned long long km = c == CRIT_NEW ? mask : dmask;
+    mk = L.crit[i] != 0;
+    if (!mk) {
       int x[4][3];
       load_tet(L.v, i, x);
       for (int a = 0; a < 4 && !mk; ++a)
         for (int b = a + 1; b < 4 && !mk; ++b) {
           const int s0 = x[a][0] + x[b][0], s1 = x[a][1] + x[b][1], s2 = x[a][2] + x[b][2];
           if ((s0 | s1 | s2) & 1) continue;        // off the lattice: not a vertex
-          mk = hset_find(K, km, pack3(s0 >> 1, s1 >> 1, s2 >> 1)) >= 0;
+          const unsigned long long key = pack3(s0 >> 1, s1 >> 1, s2 >> 1);
+          mk = bloom_may_hold(bloom, key) && hset_find(keys, mask, key) >= 0;
         }
     }
-    if (c == CRIT_NEW && !mk) L.crit[i] = CRIT_OLD;
     marks[i] = mk ? 1 : 0;
   }
   const unsigned b = __ballot_sync(~0u, mk);
@@ -861,17 +882,16 @@ __device__ __forceinline__ void bisect(const int x[4][3], int k, int w, int y[4]
 // second is appended at n + its parent's rank among the split leaves, so a round
 // touches only the leaves it splits (APPEND true; the appended leaves are put
 // in order after the last round).  The new vertices go to the vertex set and
-// to this round's set dkeys.
+// its filter.
 template <bool APPEND>
 __global__ void k_split(LeafPtrs S, long long n, const unsigned long long* marks, const unsigned long long* pos,
                         LeafPtrs D, long long* newlist, unsigned long long* keys, unsigned long long mask,
-                        unsigned long long* dkeys, unsigned long long dmask, unsigned long long* vcount,
-                        NodePtrs arch, long long abase) {
+                        Bloom bloom, unsigned long long* vcount, NodePtrs arch, long long abase) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (APPEND && !marks[i]) return;
   const long long before = (long long)pos[i];
   if (!marks[i]) {
-    if (APPEND) return;
     const long long j = i + before;
     D.v[3 * j] = S.v[3 * i]; D.v[3 * j + 1] = S.v[3 * i + 1]; D.v[3 * j + 2] = S.v[3 * i + 2];
     D.code[j] = S.code[i]; D.tag[j] = S.tag[i]; D.crit[j] = S.crit[i];
@@ -902,7 +922,7 @@ __global__ void k_split(LeafPtrs S, long long n, const unsigned long long* marks
   }
   const unsigned long long key = pack3((x[0][0] + x[k][0]) >> 1, (x[0][1] + x[k][1]) >> 1, (x[0][2] + x[k][2]) >> 1);
   if (hset_insert(keys, mask, key, vcount) < 0) atomicAdd(vcount + 3, 1ull);
-  if (hset_insert(dkeys, dmask, key, nullptr) < 0) atomicAdd(vcount + 3, 1ull);
+  bloom_add(bloom, key);
 }
 
 // number of the n sorted codes a[] below c
@@ -1232,9 +1252,12 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   // vertex set
   unsigned long long hcap = next_pow2(std::max<long long>(4096, 8ll * nroots));
   DevBuf<unsigned long long> hkeys(hcap), counters(4);   // counters: vertices, marks
+  DevBuf<uint32_t> bloomw(hcap / 8);                     // 4 filter bits per table slot
   TV_CUDA(cudaMemsetAsync(hkeys.p, 0xFF, hcap * 8, st));
+  TV_CUDA(cudaMemsetAsync(bloomw.p, 0, hcap / 2, st));
   TV_CUDA(cudaMemsetAsync(counters.p, 0, 4 * 8, st));
-  k_insert_vertices<<<blocks_for(nroots), TPB, 0, st>>>(A.v.p, nroots, hkeys.p, hcap - 1, counters.p);
+  k_insert_vertices<<<blocks_for(nroots), TPB, 0, st>>>(A.v.p, nroots, hkeys.p, hcap - 1, Bloom{bloomw.p, hcap / 8 - 1},
+                                                        counters.p);
   TV_LAUNCH();
 
   // a previous build of the same volume lends its node statistics
@@ -1253,8 +1276,7 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
   LookupBufs lk;
 
   Scanner scan;
-  DevBuf<unsigned long long> chunks, off, marks, pos, dkeys;
-  unsigned long long dcap = 0;                     // the last split's vertices (none before the first)
+  DevBuf<unsigned long long> chunks, off, marks, pos;
   DevBuf<int> owner;
   DevBuf<ScanDesc> desc;
   DevBuf<long long> newlist;
@@ -1272,8 +1294,8 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     marks.ensure(N + 1);
     pos.ensure(N + 1);
     TV_CUDA(cudaMemsetAsync(counters.p + 1, 0, 8, st));
-    k_mark<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, hkeys.p, hcap - 1, dcap ? dkeys.p : nullptr, dcap - 1,
-                                          marks.p, counters.p + 1);
+    k_mark<<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, hkeys.p, hcap - 1, Bloom{bloomw.p, hcap / 8 - 1}, marks.p,
+                                          counters.p + 1);
     TV_LAUNCH();
     unsigned long long hc[4];
     TV_CUDA(cudaMemcpyAsync(hc, counters.p, 32, cudaMemcpyDeviceToHost, st));
@@ -1287,12 +1309,15 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     if (2 * (hc[0] + (unsigned long long)M) > hcap) {
       const unsigned long long ncap = next_pow2(4 * (hc[0] + (unsigned long long)M));
       DevBuf<unsigned long long> nk(ncap);
+      DevBuf<uint32_t> nb(ncap / 8);
       TV_CUDA(cudaMemsetAsync(nk.p, 0xFF, ncap * 8, st));
+      TV_CUDA(cudaMemsetAsync(nb.p, 0, ncap / 2, st));
       k_rehash<<<blocks_for((long long)hcap), TPB, 0, st>>>(hkeys.p, (long long)hcap, nk.p, ncap - 1,
-                                                            counters.p + 3);
+                                                            Bloom{nb.p, ncap / 8 - 1}, counters.p + 3);
       TV_LAUNCH();
       TV_CUDA(cudaStreamSynchronize(st));
       hkeys = std::move(nk);
+      bloomw = std::move(nb);
       hcap = ncap;
     }
     TV_CUDA(cudaMemsetAsync(marks.p + N, 0, 8, st));
@@ -1305,10 +1330,6 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     if (nsorted >= 0) A.grow(N + M, N, st);
     else B.ensure(N + M);
     newlist.ensure(2 * M);
-    // this split's vertices (at most one per split leaf: the set stays under a quarter full)
-    dcap = next_pow2(std::max<long long>(1024, 4 * M));
-    dkeys.ensure(dcap);
-    TV_CUDA(cudaMemsetAsync(dkeys.p, 0xFF, dcap * 8, st));
     if ((size_t)(nint + M) > acode.n) {
       // grow the interior-node arrays (keep what they hold)
       const size_t cap = std::max<size_t>(2 * (size_t)(nint + M), 1024);
@@ -1327,11 +1348,11 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     const NodePtrs arch{acode.p, asum.p, acnt.p, amn.p, amx.p};
     if (nsorted >= 0) {
       k_split<true><<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, marks.p, pos.p, A.ptrs(), newlist.p, hkeys.p,
-                                                   hcap - 1, dkeys.p, dcap - 1, counters.p, arch, nint);
+                                                   hcap - 1, Bloom{bloomw.p, hcap / 8 - 1}, counters.p, arch, nint);
       TV_LAUNCH();
     } else {
       k_split<false><<<blocks_for(N), TPB, 0, st>>>(A.ptrs(), N, marks.p, pos.p, B.ptrs(), newlist.p, hkeys.p,
-                                                    hcap - 1, dkeys.p, dcap - 1, counters.p, arch, nint);
+                                                    hcap - 1, Bloom{bloomw.p, hcap / 8 - 1}, counters.p, arch, nint);
       TV_LAUNCH();
       std::swap(A, B);
     }
@@ -1340,7 +1361,7 @@ int build_grid(const float* density, const tg_volume_desc* vol, const tg_camera*
     stats_and_criterion(A, newlist.p, 2 * M, q.p, C, scan, chunks, off, owner, desc, st, sms, pp, lk);
   }
 
-  dkeys.alloc(0); marks.alloc(0); pos.alloc(0); newlist.alloc(0); chunks.alloc(0); off.alloc(0); owner.alloc(0);
+  bloomw.alloc(0); marks.alloc(0); pos.alloc(0); newlist.alloc(0); chunks.alloc(0); off.alloc(0); owner.alloc(0);
   desc.alloc(0); B = Leaves();
 
   // ---- the leaves in code order, in exact-size arrays ----
