@@ -258,41 +258,90 @@ __device__ __forceinline__ bool mma_done(uint64_t* bar, uint32_t& phase) {
 // ---------------------------------------------------------------------------
 // inference: R(x, d) per record; COMPOSE writes L + beta * max(R, 0) into the
 // record's L slot instead (the cached estimator)
+//
+// One block per SM holds the weights once and runs IG groups of 128 threads,
+// each with its own 128-row tile, operand buffer, TMEM accumulator (64 columns)
+// and mbarrier, so that one group's encoding and epilogues run while other
+// groups' MMAs are in flight.  Group g is warps 4g..4g+3: warp w reads TMEM
+// lanes 32 (w mod 4).. as tcgen05.ld requires, and the group synchronises on
+// its own named barrier.
 // ---------------------------------------------------------------------------
+constexpr int IG = 6;
+
 struct InferSmem {
   alignas(128) uint8_t W1[WID * ENC * 2];
   alignas(128) uint8_t W2[WID * WID * 2];
   alignas(128) uint8_t W3[WID * WID * 2];
-  alignas(128) uint8_t X[MT * ENC * 2];
+  alignas(128) uint8_t X[IG][MT * ENC * 2];
   float b1[WID], b2[WID], b3[WID], w4[WID];
   float b4;
-  alignas(8) uint64_t bar;
+  alignas(8) uint64_t bar[IG];
   uint32_t tmem;
 };
 
+// named barrier of one group (id 1 + g, 128 threads); returns the AND / OR of v over the group
+__device__ __forceinline__ bool group_and(int id, bool v) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.and.pred q, %2, 128, p;\n"
+               " selp.u32 %0, 1, 0, q;\n}"
+               : "=r"(r)
+               : "r"((uint32_t)v), "r"(id)
+               : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ bool group_or(int id, bool v) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, %2, 128, p;\n"
+               " selp.u32 %0, 1, 0, q;\n}"
+               : "=r"(r)
+               : "r"((uint32_t)v), "r"(id)
+               : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("barrier.cta.sync %0, 128;" ::"r"(id) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r0[16], r1[16];
+  TV_TMEM_LD16(taddr, r0);
+  TV_TMEM_LD16(taddr + 16, r1);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v[i] = __uint_as_float(r0[i]);
+    v[16 + i] = __uint_as_float(r1[i]);
+  }
+}
+
 template <bool COMPOSE>
-__global__ void __launch_bounds__(MT) k_mlp_infer(const float* __restrict__ P, float* rec, long long n,
-                                                  float* __restrict__ y) {
+__global__ void __launch_bounds__(IG * MT, 1) k_mlp_infer(const float* __restrict__ P, float* rec, long long n,
+                                                          float* __restrict__ y) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
-  const int t = threadIdx.x, warp = t >> 5;
-  if (warp == 0) tmem_alloc(&S.tmem, 64);
-  if (t == 0) mbar_init(&S.bar);
+  const int g = threadIdx.x / MT, t = threadIdx.x % MT, warp = threadIdx.x >> 5;
+  const int bid = 1 + g;                          // the group's named barrier
+  if (warp == 0) tmem_alloc(&S.tmem, 512);
+  if (threadIdx.x < IG) mbar_init(&S.bar[threadIdx.x]);
   load_matrix<false>(S.W1, P + O_W1, WID, ENC, SBO128);
   load_matrix<false>(S.W2, P + O_W2, WID, WID, SBO64);
   load_matrix<false>(S.W3, P + O_W3, WID, WID, SBO64);
-  if (t < WID) {
-    S.b1[t] = P[O_B1 + t]; S.b2[t] = P[O_B2 + t]; S.b3[t] = P[O_B3 + t]; S.w4[t] = P[O_W4 + t];
+  if (threadIdx.x < WID) {
+    const int c = threadIdx.x;
+    S.b1[c] = P[O_B1 + c]; S.b2[c] = P[O_B2 + c]; S.b3[c] = P[O_B3 + c]; S.w4[c] = P[O_W4 + c];
   }
-  if (t == 0) S.b4 = P[O_B4];
+  if (threadIdx.x == 0) S.b4 = P[O_B4];
   tc_before();
   __syncthreads();
   tc_after();
-  const uint32_t D = S.tmem, Drow = D + ((uint32_t)(warp * 32) << 16);
+  uint8_t* X = S.X[g];
+  uint64_t* bar = &S.bar[g];
+  const uint32_t D = S.tmem + (uint32_t)(g * 64), Drow = D + ((uint32_t)((warp & 3) * 32) << 16);
   uint32_t phase = 0;
   bool ok = true;
   const long long ntiles = (n + MT - 1) / MT;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (long long tile = (long long)blockIdx.x * IG + g; tile < ntiles; tile += (long long)gridDim.x * IG) {
     const long long row = tile * MT + t;
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
     if (row < n) {
@@ -301,30 +350,44 @@ __global__ void __launch_bounds__(MT) k_mlp_infer(const float* __restrict__ P, f
     }
     // a cached frame's tile without a single query (every path ended before its
     // cache collision) needs no network: its records already hold their estimates
-    if (COMPOSE && !__syncthreads_or(r0.w > 0.f)) continue;
+    if (COMPOSE && !group_or(bid, r0.w > 0.f)) continue;
     const float x[3] = {r0.x, r0.y, r0.z}, d[3] = {r1.x, r1.y, r1.z};
-    encode(x, d, [&](int c, const float* v) { put8(S.X, t, 8 * c, SBO128, v); });
-    float v[64];
+    encode(x, d, [&](int c, const float* v) { put8(X, t, 8 * c, SBO128, v); });
+    float out = S.b4;
     // three hidden layers; the first reads the 128-wide encoding
 #pragma unroll 1
     for (int layer = 0; layer < 3; ++layer) {
-      operands_ready();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_before();
+      group_sync(bid);
+      tc_after();
       if (t == 0) {
-        if (layer == 0) gemm(D, S.X, SBO128, S.W1, SBO128, ENC / 16, idesc_bf16(MT, WID), false);
-        else gemm(D, S.X, SBO64, layer == 1 ? S.W2 : S.W3, SBO64, WID / 16, idesc_bf16(MT, WID), false);
-        mma_commit(&S.bar);
+        if (layer == 0) gemm(D, X, SBO128, S.W1, SBO128, ENC / 16, idesc_bf16(MT, WID), false);
+        else gemm(D, X, SBO64, layer == 1 ? S.W2 : S.W3, SBO64, WID / 16, idesc_bf16(MT, WID), false);
+        mma_commit(bar);
       }
-      ok = mma_done(&S.bar, phase) && ok;
+      const bool mine = mbar_wait(bar, phase);
+      phase ^= 1u;
+      ok = group_and(bid, mine) && ok;
+      tc_after();
       if (!ok) break;
-      tmem_ld64(Drow, v);
-      if (layer < 2) {
-        const float* b = layer == 0 ? S.b1 : S.b2;
+      // the epilogue in two halves of 32 columns (fewer live registers)
 #pragma unroll
-        for (int c = 0; c < WID; c += 8) {
-          float h[8];
+      for (int hlf = 0; hlf < 2; ++hlf) {
+        float v[32];
+        tmem_ld32(Drow + 32u * hlf, v);
+        if (layer < 2) {
+          const float* b = (layer == 0 ? S.b1 : S.b2) + 32 * hlf;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) h[j] = fmaxf(v[c + j] + b[c + j], 0.f);
-          put8(S.X, t, c, SBO64, h);
+          for (int c = 0; c < 32; c += 8) {
+            float h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = fmaxf(v[c + j] + b[c + j], 0.f);
+            put8(X, t, 32 * hlf + c, SBO64, h);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) out += S.w4[32 * hlf + c] * fmaxf(v[c] + S.b3[32 * hlf + c], 0.f);
         }
       }
     }
@@ -335,19 +398,18 @@ __global__ void __launch_bounds__(MT) k_mlp_infer(const float* __restrict__ P, f
       }
       break;
     }
-    float out = S.b4;
-#pragma unroll
-    for (int c = 0; c < WID; ++c) out += S.w4[c] * fmaxf(v[c] + S.b3[c], 0.f);
     if (row < n) {
       if (COMPOSE) rec[8 * row + 7] = r1.w + r0.w * fmaxf(out, 0.f);
       else y[row] = out;
     }
+    // the next tile's operands overwrite X: every thread of the group is past its last read
+    // of it (the layer-3 MMA has completed; the epilogue reads TMEM only)
   }
   tc_before();
   __syncthreads();
   if (warp == 0) {
     tc_after();
-    tmem_dealloc(D, 64);
+    tmem_dealloc(S.tmem, 512);
   }
   if (!ok && t == 0) atomicAdd(&g_timeouts, 1ull);
 }
@@ -632,31 +694,10 @@ void launch_infer(const float* P, float* rec, long long n, float* y, cudaStream_
   const size_t shm = sizeof(InferSmem);
   // per device and cheap: set on every launch
   TV_CUDA(cudaFuncSetAttribute(k_mlp_infer<COMPOSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  TV_CUDA(cudaFuncSetAttribute(k_mlp_infer<COMPOSE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared));
-  int per_sm = 0;
-  TV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_infer<COMPOSE>, MT, shm));
-  // The occupancy query answered one block per SM on GB300 although three fit (66.7 KB of
-  // shared memory and 106 registers per thread each); blocks that share an SM overlap one
-  // tile's epilogue with another's MMAs, so size the grid from the kernel's own footprint too.
-  {
-    int dev = 0, smem_sm = 0, reserved = 0;
-    cudaFuncAttributes fa;
-    TV_CUDA(cudaGetDevice(&dev));
-    TV_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    TV_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
-    TV_CUDA(cudaFuncGetAttributes(&fa, k_mlp_infer<COMPOSE>));
-    const int by_smem = smem_sm / ((int)shm + (int)fa.sharedSizeBytes + reserved);
-    const int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * MT) : 1;
-    const int fit = by_smem < by_regs ? by_smem : by_regs;
-    if (fit > per_sm) per_sm = fit;
-  }
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 8) per_sm = 8;                   // 8 x 64 TMEM columns fill an SM's 512
   const long long ntiles = (n + MT - 1) / MT;
-  long long blocks = (long long)sm_count() * per_sm;
-  if (blocks > ntiles) blocks = ntiles;
-  k_mlp_infer<COMPOSE><<<(unsigned)blocks, MT, shm, st>>>(P, rec, n, y);
+  long long blocks = sm_count();                 // one block per SM: it holds all 512 TMEM columns
+  if (blocks > (ntiles + IG - 1) / IG) blocks = (ntiles + IG - 1) / IG;
+  k_mlp_infer<COMPOSE><<<(unsigned)blocks, IG * MT, shm, st>>>(P, rec, n, y);
   TV_LAUNCH();
 }
 
