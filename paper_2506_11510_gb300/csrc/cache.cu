@@ -192,6 +192,18 @@ __device__ void load_matrix(uint8_t* dst, const float* M, int rows, int K, uint3
 // ---------------------------------------------------------------------------
 // the frequency encoding, 8 features at a time: chunk c covers features 8c..8c+7
 // ---------------------------------------------------------------------------
+// sin(pi u) and cos(pi u): with k = rint(u), u - k is exact and sin(pi u) =
+// (-1)^k sin(pi (u - k)), cos(pi u) = (-1)^k cos(pi (u - k)); the angle is in
+// [-pi/2, pi/2], where the hardware approximations' absolute error is below
+// 2^-21 -- far below the bf16 rounding the features go through (2^-9 relative).
+__device__ __forceinline__ void sincospi_enc(float u, float* s, float* c) {
+  const float k = rintf(u);
+  const float th = (u - k) * 3.14159265358979f;
+  const uint32_t odd = ((uint32_t)__float2int_rn(k) & 1u) << 31;
+  *s = __uint_as_float(__float_as_uint(__sinf(th)) ^ odd);
+  *c = __uint_as_float(__float_as_uint(__cosf(th)) ^ odd);
+}
+
 template <class Sink>
 __device__ __forceinline__ void encode(const float x[3], const float d[3], Sink&& sink) {
 #pragma unroll
@@ -206,10 +218,10 @@ __device__ __forceinline__ void encode(const float x[3], const float d[3], Sink&
       else if (p == 2) { a = d[1]; b = d[2]; }
       else if (p < 3 + 3 * PFREQ) {
         const int q = p - 3;                    // sin and cos of 2^l pi x_a
-        sincospif(x[q / PFREQ] * (float)(1 << (q % PFREQ)), &a, &b);
+        sincospi_enc(x[q / PFREQ] * (float)(1 << (q % PFREQ)), &a, &b);
       } else if (p < 3 + 3 * PFREQ + 3 * DFREQ) {
         const int q = p - 3 - 3 * PFREQ;        // sin and cos of 2^l pi d_a
-        sincospif(d[q / DFREQ] * (float)(1 << (q % DFREQ)), &a, &b);
+        sincospi_enc(d[q / DFREQ] * (float)(1 << (q % DFREQ)), &a, &b);
       } else {
         a = b = 0.f;
       }
