@@ -676,11 +676,11 @@ def cache_leg(args, s, grid, dev, plain_ms):
            "reference_ms": round(ref_ms, 1), "rms_radiance": round(rel, 6),
            "plain": {"spp": s.spp, "ms": round(plain_ms, 2), "rmse": round(target, 6)}, "variants": []}
 
-    def variant(rounds, depth, train_bounces=None, seed_k=0, survive=0.0):
+    def variant(rounds, depth, train_bounces=None, seed_k=0, survive=0.0, rfrom=0):
         # seed_k selects the initial weights and the training paths (their pixels and random streams)
         rc = RC.RadianceCache(W.mlp_init_params(1 + seed_k, b4=0.1), device=dev, lr=3e-3)
         _, train_ms = timed(lambda: rc.train(grid, s.camera, s.medium, s.render_seed + 7919 * seed_k, rounds=rounds,
-                                             max_bounces=train_bounces, survive=survive))
+                                             max_bounces=train_bounces, survive=survive, roulette_from=rfrom))
         curve, reached = [], None
         for spp in (1, 2, 4, 8, 16, 32):
             (img, _), ms = timed(lambda: rc.render(grid, s.camera, s.medium, spp, s.render_seed, depth))
@@ -692,13 +692,14 @@ def cache_leg(args, s, grid, dev, plain_ms):
                 "final_train_loss": round(float(rc.loss[2]), 6), "curve": curve,
                 "time_to_equal_rmse_ms": None if reached is None else round(reached, 2)}
 
-    def seeds(rounds, depth, train_bounces=None, n=3, survive=0.0):
-        runs = [variant(rounds, depth, train_bounces, k, survive) for k in range(n)]
+    def seeds(rounds, depth, train_bounces=None, n=3, survive=0.0, rfrom=0):
+        runs = [variant(rounds, depth, train_bounces, k, survive, rfrom) for k in range(n)]
         t = [r["time_to_equal_rmse_ms"] for r in runs]
         ok = sorted(x for x in t if x is not None)
         med = statistics.median(t) if len(ok) == len(t) else None
         return {"cache_depth": depth, "train_rounds": rounds, "train_samples_per_round": (1 << 14) * 4,
                 "train_max_bounces": train_bounces or s.medium.max_bounces, "train_survive": survive,
+                "train_roulette_from": rfrom,
                 "seeds": len(runs),
                 "reached": len(ok), "time_to_equal_rmse_ms_median": None if med is None else round(med, 2),
                 "time_to_equal_rmse_ms_min": ok[0] if ok else None,
@@ -719,6 +720,10 @@ def cache_leg(args, s, grid, dev, plain_ms):
     res["fixed_configuration"] = summary(fixed)
     fixed_rr = seeds(8, 1, survive=0.5)
     res["fixed_configuration_roulette"] = summary(fixed_rr)
+    # A third configuration, fixed before its first measurement: the same roulette (survival 1/2)
+    # played only from collision 16 (0-based) on, so that it cuts only the long tail of training
+    # paths (3.1 collisions per path on average), which sets the training trace's time
+    res["fixed_configuration_late_roulette"] = summary(seeds(8, 1, survive=0.5, rfrom=16))
     res["roulette_variants"] = [summary(seeds(8, 1, survive=0.75)), summary(seeds(32, 1, survive=0.5))]
     # the other training budgets and depths, for context (each the median of 3 seeds as well)
     for rounds in [int(r) for r in str(args.cache_train_rounds).split(",") if r]:

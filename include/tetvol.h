@@ -392,12 +392,15 @@ int tg_random_paths(uint64_t seed, int64_t n, int32_t width, int32_t height, int
  * survive (the draw after collision b is slot b of Philox stream 0x10000, counter
  * (sample, b / 4, 0x10000, 0)) and its throughput is divided by survive, so every
  * target keeps its expectation while the paths end sooner; 0 or 1: no roulette.
+ * roulette_from >= 0: the roulette is played only after collisions b >= roulette_from
+ * (0-based), so only paths longer than that are cut; 0: after every collision
+ * past the last sample.
  * Asynchronous; each call takes its own scratch on its stream.
- * TG_EINVAL for survive outside [0, 1].
+ * TG_EINVAL for survive outside [0, 1] or a negative roulette_from.
  */
 int tet_cache_samples(const tg_grid* g, const tg_camera* cam, const tg_medium* med, uint64_t seed, int64_t n,
                       const int32_t* px, const int32_t* py, const int32_t* sample, int32_t max_vertices,
-                      float* samples, float* L, float survive, void* cuda_stream);
+                      float* samples, float* L, float survive, int32_t roulette_from, void* cuda_stream);
 
 /*
  * tet_cache_queries - the cached estimator's paths for n listed paths: a path

@@ -184,10 +184,11 @@ class Grid:
         return out
 
     def cache_paths(self, camera, medium, seed, px, py, sample, cache_depth=0, max_vertices=0, nthreads=0,
-                    survive=0.0):
+                    survive=0.0, roulette_from=0):
         """The radiance cache's uses of the tracer: cached-path records (cache_depth > 0,
         query [n][8]) and training samples from path vertices (vertices [n][max_vertices][8]);
-        survive in (0, 1): Russian roulette after the last training vertex."""
+        survive in (0, 1): Russian roulette after the last training vertex, at collisions
+        roulette_from and later (0-based)."""
         px = np.ascontiguousarray(px, np.int32); py = np.ascontiguousarray(py, np.int32)
         sm = np.ascontiguousarray(sample, np.int32)
         n = len(px)
@@ -196,7 +197,8 @@ class Grid:
         L = np.empty(n, np.float64); flags = np.empty(n, np.int32)
         _check(lib().orc_cache_paths(self._h, C.byref(camera_struct(camera)), C.byref(medium_struct(medium)),
                                      C.c_uint64(seed), C.c_int64(n), _p(px), _p(py), _p(sm), cache_depth, _p(q),
-                                     max_vertices, _p(v), _p(L), _p(flags), C.c_float(survive), nthreads))
+                                     max_vertices, _p(v), _p(L), _p(flags), C.c_float(survive),
+                                     int(roulette_from), nthreads))
         return dict(query=q, vertices=v, L=L, flags=flags)
 
     def channels(self, density, temperature=None, albedo=None, aniso=None, nthreads=0):

@@ -866,6 +866,7 @@ struct CacheIO {
   int vcap = 0;                // vertices recorded per path
   double* vtx = nullptr;       // [vcap][8]: x (3), target, d (3), valid
   float survive = 0.0f;        // in (0, 1): Russian roulette once all vcap vertices are recorded
+  int roulette_from = 0;       // ... and only at collisions b >= roulette_from (0-based)
 };
 
 // Russian roulette on a training path after its last training vertex: before
@@ -874,6 +875,8 @@ struct CacheIO {
 // every target -- is unchanged, while the path ends after about 1 / (1 - q)
 // more collisions instead of running to the bounce limit.  The decision after
 // collision b is slot b of its own Philox stream, so it shifts no other draw.
+// With a start collision r, only collisions b >= r play it: paths shorter than
+// r are untouched and only the long tail is cut.
 const uint32_t ROULETTE_STREAM = 0x10000u;
 
 // Sec. 3, Algorithm 1 "Trace", with the estimator around it: throughput beta
@@ -952,7 +955,8 @@ PathOut trace(const Cells& cells, const Domain& D, const Locate& locate_fn, cons
       }
       break;
     }
-    if (cache && cache->vcap > 0 && nv >= cache->vcap && cache->survive > 0.0f && cache->survive < 1.0f) {
+    if (cache && cache->vcap > 0 && nv >= cache->vcap && b >= cache->roulette_from && cache->survive > 0.0f &&
+        cache->survive < 1.0f) {
       const double q = (double)cache->survive;
       if (uniform(seed, pixel, (uint32_t)sample, (uint32_t)b, ROULETTE_STREAM) >= q) { out.flags |= 32; break; }
       beta /= q;
@@ -1212,10 +1216,10 @@ int orc_render_paths(const orc_grid* g, const orc_camera* cam, const orc_medium*
 int orc_cache_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* med, uint64_t seed, int64_t n,
                     const int32_t* px, const int32_t* py, const int32_t* sample, int32_t cache_depth,
                     double* query, int32_t max_vertices, double* vertices, double* L, int32_t* flags,
-                    float survive, int32_t nthreads) {
+                    float survive, int32_t roulette_from, int32_t nthreads) {
   if (!g || !valid_camera(cam) || !valid_medium(med) || n < 0 || cache_depth < 0 || max_vertices < 0 ||
       max_vertices > 64 || (max_vertices > 0 && !vertices) || (cache_depth > 0 && !query) ||
-      !(survive >= 0.0f && survive <= 1.0f))
+      !(survive >= 0.0f && survive <= 1.0f) || roulette_from < 0)
     return EINVAL_;
   TetCells cells = {g, (double)med->sigma_scale * g->D.cube};
   CamRay cr = camera_rays(cam, g->D);
@@ -1229,6 +1233,7 @@ int orc_cache_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* 
     io.vcap = max_vertices;
     io.vtx = max_vertices > 0 ? vertices + 8 * max_vertices * i : nullptr;
     io.survive = survive;
+    io.roulette_from = roulette_from;
     PathOut o = trace(cells, g->D, loc, cr, med, seed, px[i], py[i], sample[i], nullptr, 0, &io);
     if (L) L[i] = o.L;
     if (flags) flags[i] = o.flags;

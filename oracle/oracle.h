@@ -73,11 +73,13 @@ int orc_render_paths(const orc_grid* g, const orc_camera* cam, const orc_medium*
  *  survive in (0, 1): once a path has recorded its max_vertices vertices, Russian
  *    roulette before every further scattering -- the path goes on with probability
  *    survive (the draw after collision b is slot b of Philox stream 0x10000) and its
- *    throughput is divided by survive; 0 or 1: no roulette. */
+ *    throughput is divided by survive; 0 or 1: no roulette.
+ *  roulette_from >= 0: the roulette is played only after collisions b >= roulette_from
+ *    (0-based); 0: after every collision past the last vertex. */
 int orc_cache_paths(const orc_grid* g, const orc_camera* cam, const orc_medium* med, uint64_t seed,
                     int64_t n, const int32_t* px, const int32_t* py, const int32_t* sample,
                     int32_t cache_depth, double* query, int32_t max_vertices, double* vertices,
-                    double* L, int32_t* flags, float survive, int32_t nthreads);
+                    double* L, int32_t* flags, float survive, int32_t roulette_from, int32_t nthreads);
 int orc_render(const orc_grid* g, const orc_camera* cam, const orc_medium* med, int32_t spp,
                uint64_t seed, int32_t sample_offset, double* sum, double* sumsq, int64_t* steps,
                int32_t nthreads);

@@ -78,7 +78,7 @@ SIGNATURES = {
     "tg_batch_free": (None, [_VP]),
     "tg_random_paths": (C.c_int, [_U64, _I64, _I32, _I32, _I32, _VP, _VP, _VP, _VP]),
     "tet_cache_samples": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _U64, _I64, _VP, _VP, _VP, _I32,
-                                    _VP, _VP, C.c_float, _VP]),
+                                    _VP, _VP, C.c_float, _I32, _VP]),
     "tet_cache_queries": (C.c_int, [_VP, C.POINTER(TgCamera), C.POINTER(TgMedium), _U64, _I64, _VP, _VP, _VP, _I32,
                                     _VP, _VP]),
     "rc_mlp_infer": (C.c_int, [_VP, _VP, _I64, _VP, _VP]),

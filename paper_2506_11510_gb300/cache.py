@@ -32,9 +32,10 @@ def random_paths(seed: int, n: int, width: int, height: int, sample_base: int, d
 
 
 def cache_samples(grid: Grid, camera, medium, seed: int, px, py, sample, max_vertices: int, out=None,
-                  want_L: bool = False, survive: float = 0.0):
+                  want_L: bool = False, survive: float = 0.0, roulette_from: int = 0):
     """Training samples [n * max_vertices][8] (x, target, d, valid) from full paths;
-    survive in (0, 1): Russian roulette after a path's last training vertex."""
+    survive in (0, 1): Russian roulette after a path's last training vertex, played
+    after collisions roulette_from and later (0-based)."""
     px, py, sm, dev = _paths(px, py, sample)
     n = px.numel()
     samples = out if out is not None else torch.empty((n * max_vertices, 8), dtype=torch.float32, device=dev)
@@ -42,7 +43,8 @@ def cache_samples(grid: Grid, camera, medium, seed: int, px, py, sample, max_ver
     L = torch.empty(n, dtype=torch.float32, device=dev) if want_L else None
     N.check(N.lib().tet_cache_samples(grid.handle, C.byref(camera_struct(camera)), C.byref(medium_struct(medium)),
                                       C.c_uint64(seed), n, _ptr(px), _ptr(py), _ptr(sm), int(max_vertices),
-                                      _ptr(samples), _ptr(L), float(survive), _stream()), "tet_cache_samples")
+                                      _ptr(samples), _ptr(L), float(survive), int(roulette_from), _stream()),
+            "tet_cache_samples")
     return (samples, L) if want_L else samples
 
 
@@ -141,7 +143,7 @@ class RadianceCache:
 
     def train(self, grid: Grid, camera, medium, seed: int, rounds: int = 1, first_round: int = 0,
               n_paths: int = 1 << 14, max_vertices: int = 4, batches: int = 4, sample_base: int = 1 << 24,
-              max_bounces: Optional[int] = None, survive: float = 0.0):
+              max_bounces: Optional[int] = None, survive: float = 0.0, roulette_from: int = 0):
         """`rounds` training rounds: each traces n_paths full paths at uniform
         pixels (sample indices disjoint from rendering's) and takes `batches`
         Adam steps on their n_paths * max_vertices vertex samples.  The paths
@@ -151,7 +153,8 @@ class RadianceCache:
         for the longest paths of the medium's own limit).  survive in (0, 1)
         ends the training paths sooner without biasing them: after their last
         training vertex they go on with that probability, throughput divided
-        by it (Russian roulette)."""
+        by it (Russian roulette); roulette_from > 0 plays it only after that
+        collision (0-based), so that only the long tail of paths is cut."""
         if max_bounces is not None:
             medium = with_max_bounces(medium, max_bounces)
         total = rounds * n_paths
@@ -162,7 +165,8 @@ class RadianceCache:
         if self._buf is None or self._buf.shape[0] < nslot:
             self._buf = torch.empty((nslot, 8), dtype=torch.float32, device=self.params.device)
         buf = self._buf[:nslot]
-        cache_samples(grid, camera, medium, seed, px, py, sm, max_vertices, out=buf, survive=survive)
+        cache_samples(grid, camera, medium, seed, px, py, sm, max_vertices, out=buf, survive=survive,
+                      roulette_from=roulette_from)
         per_round = n_paths * max_vertices
         per = (per_round + batches - 1) // batches
         for r in range(rounds):

@@ -738,9 +738,9 @@ int tg_random_paths(uint64_t seed, int64_t n, int32_t width, int32_t height, int
 
 int tet_cache_samples(const tg_grid* g, const tg_camera* cam, const tg_medium* med, uint64_t seed, int64_t n,
                       const int32_t* px, const int32_t* py, const int32_t* sample, int32_t max_vertices,
-                      float* samples, float* L, float survive, void* cuda_stream) {
+                      float* samples, float* L, float survive, int32_t roulette_from, void* cuda_stream) {
   if (!g || !camera_ok(cam) || !medium_ok(med) || n < 0 || max_vertices < 1 || max_vertices > 64 ||
-      (n > 0 && (!px || !py || !sample || !samples)) || !(survive >= 0.f && survive <= 1.f))
+      (n > 0 && (!px || !py || !sample || !samples)) || !(survive >= 0.f && survive <= 1.f) || roulette_from < 0)
     return TG_EINVAL;
   try {
     const GridImpl& G = g->impl;
@@ -757,6 +757,7 @@ int tet_cache_samples(const tg_grid* g, const tg_camera* cam, const tg_medium* m
     ep.vtx_cap = max_vertices;
     ep.vtx = samples;
     ep.survive = survive;
+    ep.roulette_from = roulette_from;
     run_tet<MODE_TRACE>(G, ep, st);
   } catch (const Error& e) {
     return e.code;

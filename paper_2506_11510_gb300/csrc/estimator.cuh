@@ -114,6 +114,7 @@ struct EstParams {
   int vtx_cap;                              // trace mode: training samples from the first vtx_cap collisions
   float* vtx;                               // [path][vtx_cap][8]: x (3), target, d (3), valid
   float survive;                            // in (0, 1): Russian roulette after the last training vertex
+  int roulette_from;                        // ... played after collisions >= this one (0-based)
   float ext[3];                             // domain extent in grid units (positions are stored over it)
   // extended medium (EXT instantiations): extra per-cell channels, voxel medium
   int ext_flags;                            // 1 emission, 2 per-cell albedo, 4 per-cell g, 8 voxel medium
@@ -542,14 +543,16 @@ __global__ void __launch_bounds__(EST_BLOCK, TV_EST_MIN_BLOCKS) k_estimate(const
           r[1] = make_float4(d.x.hi, d.y.hi, d.z.hi, ff_float(L));
           queried = true;
           finish();
-        } else if (TRACE && ep.vtx && nv >= ep.vtx_cap && ep.survive > 0.f && ep.survive < 1.f &&
+        } else if (TRACE && ep.vtx && nv >= ep.vtx_cap && bounce >= ep.roulette_from && ep.survive > 0.f &&
+                   ep.survive < 1.f &&
                    rng_u(seedv(), pixel, sample, (uint32_t)bounce, ROULETTE_STREAM) >= ep.survive) {
           // a training path past its last training vertex ends by Russian roulette
           flags |= 32;
           finish();
         } else {
           // (a training path that survives the roulette carries throughput / survive)
-          if (TRACE && ep.vtx && nv >= ep.vtx_cap && ep.survive > 0.f && ep.survive < 1.f)
+          if (TRACE && ep.vtx && nv >= ep.vtx_cap && bounce >= ep.roulette_from && ep.survive > 0.f &&
+              ep.survive < 1.f)
             beta = __fdiv_rn(beta, ep.survive);
           // SamplePhaseFunction, then a new free flight from the collision point
           const float3 nd = hg_scatter(gg, rng_u(seedv(), pixel, sample, 3 + 3 * bounce),

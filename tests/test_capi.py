@@ -78,11 +78,13 @@ def test_radiance_cache_argument_checks_need_no_gpu():
                                None) == N.TG_EINVAL                                               # depth 0
     assert L.tet_cache_queries(fake, C.byref(cam), C.byref(med), 0, 4, fake, fake, fake, 0, fake,
                                None) == N.TG_EINVAL
-    assert L.tet_cache_samples(fake, C.byref(cam), C.byref(med), 0, 4, fake, fake, fake, 65, fake, None, 0.0,
+    assert L.tet_cache_samples(fake, C.byref(cam), C.byref(med), 0, 4, fake, fake, fake, 65, fake, None, 0.0, 0,
                                None) == N.TG_EINVAL                                               # > 64 vertices
     for q in (-0.5, 1.5, float("nan")):                                                           # survival
-        assert L.tet_cache_samples(fake, C.byref(cam), C.byref(med), 0, 4, fake, fake, fake, 4, fake, None, q,
+        assert L.tet_cache_samples(fake, C.byref(cam), C.byref(med), 0, 4, fake, fake, fake, 4, fake, None, q, 0,
                                    None) == N.TG_EINVAL
+    assert L.tet_cache_samples(fake, C.byref(cam), C.byref(med), 0, 4, fake, fake, fake, 4, fake, None, 0.5, -1,
+                               None) == N.TG_EINVAL                                               # roulette start
     assert L.tg_random_paths(0, 4, 0, 8, 0, fake, fake, fake, None) == N.TG_EINVAL
     assert L.tg_random_paths(0, 4, 8, 8, (1 << 31) - 2, fake, fake, fake, None) == N.TG_EINVAL
     assert L.rc_mlp_grad(fake, fake, 0, fake, fake, None) == N.TG_OK                              # nothing to do

@@ -323,3 +323,59 @@ def test_roulette_keeps_the_targets_unbiased(tiny_grid):
     dL = b["L"] - a["L"]
     assert abs(dL.mean()) <= 4 * dL.std() / math.sqrt(dL.size)
     assert ((b["flags"] & 32) != 0).mean() > 0.05
+
+
+def test_roulette_start_beyond_every_path_is_the_plain_path(tiny_grid):
+    """A roulette that starts at the bounce limit never plays: the same vertices,
+    targets, estimates and flags as without it."""
+    s = W.scene("tiny")
+    px, py, sm = all_paths(s.camera, 1)
+    plain = tiny_grid.cache_paths(s.camera, s.medium, 7, px, py, sm, max_vertices=2)
+    r = tiny_grid.cache_paths(s.camera, s.medium, 7, px, py, sm, max_vertices=2, survive=0.5,
+                              roulette_from=s.medium.max_bounces)
+    assert np.array_equal(r["vertices"], plain["vertices"]) and np.array_equal(r["L"], plain["L"])
+    assert np.array_equal(r["flags"], plain["flags"])
+
+
+def test_roulette_start_collision():
+    """Furnace (albedo 1, environment 1, no sun), 2 training vertices, bounce limit 5,
+    roulette from collision 3: it is played once, after collision 3 (index), by the
+    paths that get that far, so an escaping path returns exactly 1 (escaped before)
+    or 1 / q (survived it) -- never 1 / q^2, as it would with roulettes after
+    collisions 1 and 2 -- a killed one 0; the kill rate is 1 - q (binomial, 4 sd)."""
+    q = 0.375
+    vol = np.full((16, 16, 16), 0.5, np.float32)
+    g = O.Grid(vol, (0, 0, 0), 1 / 16, theta=-1, max_depth=6)
+    cam = W.Camera((0.5, 0.5, -1.5), (0.5, 0.5, 0.5), (0, 1, 0), 40.0, 64, 64)
+    med = W.Medium(1.0, 0.3, 8.0, 5, (0, -1, 0), 0.0, 1.0)
+    px, py, sm = all_paths(cam, 16)
+    r = g.cache_paths(cam, med, 9, px, py, sm, max_vertices=2, survive=q, roulette_from=3)
+    killed = (r["flags"] & 32) != 0
+    trunc = (r["flags"] & 2) != 0
+    early = ~killed & ~trunc & (r["L"] == 1.0)
+    played = ~early & ((r["flags"] & 4) == 0)        # (flag 4: missed the box)
+    assert np.all(r["L"][killed] == 0) and np.all(r["L"][trunc] == 0)
+    assert np.all(np.isin(r["L"][played & ~killed & ~trunc], [1.0 / q]))
+    n, k = int(played.sum()), int(killed.sum())
+    assert n > 3000
+    assert abs(k - n * (1 - q)) <= 4 * math.sqrt(n * q * (1 - q))
+
+
+def test_roulette_from_a_later_collision_keeps_the_targets_unbiased(tiny_grid):
+    """As the roulette after the last vertex, but played from collision 2 on (1
+    training vertex): the mean target difference is zero within 4 sd / sqrt(n), and
+    paths ending by the roulette never do so before collision 2."""
+    s = W.scene("tiny")
+    px, py, sm = all_paths(s.camera, 16)
+    med = W.Medium(0.9, 0.3, 30.0, 64, s.medium.sun_dir, s.medium.sun_irradiance, 0.5)
+    a = tiny_grid.cache_paths(s.camera, med, 13, px, py, sm, max_vertices=1)
+    b = tiny_grid.cache_paths(s.camera, med, 13, px, py, sm, max_vertices=1, survive=0.5, roulette_from=2)
+    c = tiny_grid.cache_paths(s.camera, med, 13, px, py, sm, max_vertices=1, survive=0.5)
+    v = a["vertices"][:, 0, 7] == 1
+    d = b["vertices"][v, 0, 3] - a["vertices"][v, 0, 3]
+    assert v.sum() > 5000 and np.any(d != 0)
+    assert abs(d.mean()) <= 4 * d.std() / math.sqrt(d.size)
+    # fewer paths end by the roulette when it starts later, and the rest of every path
+    # up to collision 2 is the plain one's
+    assert 0 < ((b["flags"] & 32) != 0).sum() < ((c["flags"] & 32) != 0).sum()
+    assert not np.array_equal(b["L"], c["L"])
