@@ -397,8 +397,9 @@ __device__ __forceinline__ void face_planes32(const int x[4][3], int nrm[4][3], 
   }
 }
 
-// Statistics of a leaf whose box is small (small_box), by one thread.
-template <bool BOX>
+// Statistics of a leaf whose box is small (small_box), by one thread (QUAD: rows
+// start on 16-byte boundaries, and each row's voxels are read as aligned 16-byte quads).
+template <bool BOX, bool QUAD>
 __device__ __forceinline__ void small_box_stats(const int lo[3], const int hi[3], const int nrm[4][3],
                                                 const int rhs[4], const uint32_t* __restrict__ q, const Geo& g,
                                                 uint32_t& cnt, unsigned long long& sum, uint32_t& mn, uint32_t& mx) {
@@ -409,9 +410,21 @@ __device__ __forceinline__ void small_box_stats(const int lo[3], const int hi[3]
       int xa = lo[0], xb = hi[0];
       if (!BOX) row_interval(nrm, rhs, hs, jj, kk, lo[0], hi[0], &xa, &xb);
       const uint32_t* row = q + ((size_t)kk * g.ny + jj) * g.nx;
-      for (int ii = xa; ii <= xb; ++ii) {
-        const uint32_t v = __ldg(row + ii);
-        ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+      if (QUAD) {
+        for (int qd = xa >> 2; qd <= (xb >> 2) && xa <= xb; ++qd) {
+          const uint4 v4 = __ldg(reinterpret_cast<const uint4*>(row) + qd);
+          const uint32_t w[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int xx = 4 * qd + e;
+            if (xx >= xa && xx <= xb) { ++cnt; sum += w[e]; mn = min(mn, w[e]); mx = max(mx, w[e]); }
+          }
+        }
+      } else {
+        for (int ii = xa; ii <= xb; ++ii) {
+          const uint32_t v = __ldg(row + ii);
+          ++cnt; sum += v; mn = min(mn, v); mx = max(mx, v);
+        }
       }
     }
 }
@@ -429,7 +442,7 @@ struct __align__(16) ScanDesc {
 // A3 statistics, pass 1: the statistics of a new leaf with a small voxel box
 // (by this thread), or the work items of a larger one (ROWS rows of its box
 // each) and what they share, its statistics reset for pass 2
-template <bool BOX>
+template <bool BOX, bool QUAD>
 __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo g, unsigned long long* chunks,
                              ScanDesc* desc, const uint32_t* __restrict__ q) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -446,7 +459,7 @@ __global__ void k_stats_prep(LeafPtrs L, const long long* list, long long m, Geo
     chunks[j] = 0;
     uint32_t cnt = 0, mn = 0xFFFFFFFFu, mx = 0;
     unsigned long long sum = 0;
-    if (small) small_box_stats<BOX>(lo, hi, nrm, rhs, q, g, cnt, sum, mn, mx);
+    if (small) small_box_stats<BOX, QUAD>(lo, hi, nrm, rhs, q, g, cnt, sum, mn, mx);
     L.cnt[i] = cnt; L.sum[i] = sum; L.mn[i] = mn; L.mx[i] = mx;
     return;
   }
@@ -1090,6 +1103,9 @@ struct Scanner {
   }
 };
 
+// every row of the quantised volume starts on a 16-byte boundary
+bool quad_rows(const Geo& g, const uint32_t* q) { return g.nx % 4 == 0 && reinterpret_cast<uintptr_t>(q) % 16 == 0; }
+
 // Pass 2 of the statistics over `total` work items (offsets off[0..m]): the
 // owner of every work item, then the scan.
 template <bool BOX>
@@ -1101,7 +1117,7 @@ void stats_scan(LeafPtrs L, const ScanDesc* desc, long long m, const unsigned lo
   TV_LAUNCH();
   const long long wblocks = std::min<long long>((long long)(total + (TPB / 32) - 1) / (TPB / 32), (long long)sms * 64);
   // 16-byte loads along the rows when every row starts on a 16-byte boundary
-  if (g.nx % 4 == 0 && reinterpret_cast<uintptr_t>(q) % 16 == 0)
+  if (quad_rows(g, q))
     k_stats_scan<BOX, true><<<(unsigned)wblocks, TPB, 0, st>>>(L, desc, off, owner.p, total, q, g);
   else
     k_stats_scan<BOX, false><<<(unsigned)wblocks, TPB, 0, st>>>(L, desc, off, owner.p, total, q, g);
@@ -1149,7 +1165,10 @@ void stats_and_criterion(Leaves& Lv, const long long* list, long long m, const u
     chunks.ensure(sm + 1);
     off.ensure(sm + 1);
     desc.ensure(sm);
-    k_stats_prep<false><<<blocks_for(sm), TPB, 0, st>>>(L, slist, sm, C.g, chunks.p, desc.p, q);
+    if (quad_rows(C.g, q))
+      k_stats_prep<false, true><<<blocks_for(sm), TPB, 0, st>>>(L, slist, sm, C.g, chunks.p, desc.p, q);
+    else
+      k_stats_prep<false, false><<<blocks_for(sm), TPB, 0, st>>>(L, slist, sm, C.g, chunks.p, desc.p, q);
     TV_LAUNCH();
     TV_CUDA(cudaMemsetAsync(chunks.p + sm, 0, sizeof(unsigned long long), st));
     scan.exclusive(chunks.p, off.p, sm + 1, st);
@@ -1508,8 +1527,11 @@ int grid_channels(GridImpl& G, const float* density, const float* temperature, c
     chunks.ensure(N + 1);
     off.ensure(N + 1);
     desc.ensure(N);
-    if (box) k_stats_prep<true><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p, q.p);
-    else k_stats_prep<false><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p, q.p);
+    const bool qr = quad_rows(g, q.p);
+    if (box && qr) k_stats_prep<true, true><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p, q.p);
+    else if (box) k_stats_prep<true, false><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p, q.p);
+    else if (qr) k_stats_prep<false, true><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p, q.p);
+    else k_stats_prep<false, false><<<blocks_for(N), TPB, 0, st>>>(L, nullptr, N, g, chunks.p, desc.p, q.p);
     TV_LAUNCH();
     TV_CUDA(cudaMemsetAsync(chunks.p + N, 0, sizeof(unsigned long long), st));
     scan.exclusive(chunks.p, off.p, N + 1, st);
