@@ -873,19 +873,19 @@ __global__ void k_mark(LeafPtrs L, long long n, const unsigned long long* keys, 
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(nmark, (unsigned long long)__popc(b));
 }
 
-// The two children of leaf i (Maubach bisection of its refinement edge x0 xk);
-// returns the new vertex.
+// Child w of a tet with refinement edge x0 xk (Maubach bisection, z its
+// midpoint): child 0 is the tet with xk replaced by z, child 1 drops x0, shifts
+// x1..xk down by one and puts z at position k.  Written with static indices only
+// (a select per vertex), so the vertices stay in registers.
 __device__ __forceinline__ void bisect(const int x[4][3], int k, int w, int y[4][3]) {
-  int o = 0;
-  for (int s = w; s < k + w; ++s, ++o)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) y[o][a] = x[s][a];
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-  for (int a = 0; a < 3; ++a) y[o][a] = (x[0][a] + x[k][a]) >> 1;
-  ++o;
-  for (int s = k + 1; s < 4; ++s, ++o)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) y[o][a] = x[s][a];
+    for (int a = 0; a < 3; ++a) {
+      const int z = (x[0][a] + (k == 1 ? x[1][a] : (k == 2 ? x[2][a] : x[3][a]))) >> 1;
+      const int up = i < 3 ? x[i + 1][a] : x[3][a];
+      y[i][a] = i == k ? z : ((w == 1 && i < k) ? up : x[i][a]);
+    }
 }
 
 // A4: Maubach bisection of the marked leaves.  While many leaves split, the
@@ -933,7 +933,10 @@ __global__ void k_split(LeafPtrs S, long long n, const unsigned long long* marks
     D.tag[j] = nt;
     newlist[2 * before + w] = j;
   }
-  const unsigned long long key = pack3((x[0][0] + x[k][0]) >> 1, (x[0][1] + x[k][1]) >> 1, (x[0][2] + x[k][2]) >> 1);
+  int z[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) z[a] = (x[0][a] + (k == 1 ? x[1][a] : (k == 2 ? x[2][a] : x[3][a]))) >> 1;
+  const unsigned long long key = pack3(z[0], z[1], z[2]);
   if (hset_insert(keys, mask, key, vcount) < 0) atomicAdd(vcount + 3, 1ull);
   bloom_add(bloom, key);
 }
